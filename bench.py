@@ -1,0 +1,403 @@
+#!/usr/bin/env python3
+"""Benchmark: stable Merge Path merge of the large unbalanced key-value
+workload on GB300.
+
+Workload: A = 2^28 and B = 2^26 uint64 keys, each with a uint32 payload
+(its global source index); keys uniform over the full 64-bit range, sorted
+(other distributions: --dist a_gt_b | interleaved | distinct16).  One step
+= one mp_merge_pairs call (partition kernel + merge-tile kernel) over the
+whole workload, inputs resident in HBM.  Inputs and outputs (8.05 GB per
+pass) are far larger than the 129 MB L2, so no flush is needed between
+steps.
+
+Printed (rank 0, one JSON line): Gkeys/s of merged output, the roofline of
+the merge-tile kernel (algorithmic bytes 2 * n * (8 + 4) per launch over
+its CUDA-event duration, against the measured HBM copy peak), the CPU
+oracle timed on the host, the end-to-end rate through the host-buffer C
+entry point (copies included), the SM clocks seen while timing, and the
+number of kernels launched in the timed region.
+
+--impl reference times the plain CPU oracle (the program this library is
+checked against) on a bounded sample of the same workload.
+
+Multi-GPU (torchrun): every rank merges its own copy of the workload (weak
+scaling, no data-path collective); time = max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "merge Gkeys/s & % of HBM peak; batched/served vs per-call on same GPU; p99"
+UNIT = "Gkeys/s"
+NOMINAL_HBM_GBS = 7900.0
+PEAK_FALLBACK_GBS = 6800.0
+KERNEL_SOURCES = ["paper_1406_2628_gb300/csrc/merge.cu", "paper_1406_2628_gb300/csrc/mp_tile.cuh",
+                  "paper_1406_2628_gb300/csrc/mp_device.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "merge_tile_kernel_large_kv_traffic.json")
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--dist", default="uniform", choices=["uniform", "a_gt_b", "interleaved", "distinct16"])
+    p.add_argument("--log2-a", type=int, default=28)
+    p.add_argument("--log2-b", type=int, default=26)
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--plan", default=None, help="NT,VT tile plan (default: automatic)")
+    return p.parse_args()
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return PEAK_FALLBACK_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload_key):
+    """DRAM bytes per merge-kernel launch from a committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    entry = d.get("workloads", {}).get(workload_key)
+    return None if entry is None else float(entry["traffic_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle samples every 100 ms in the background."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,"
+              "utilization.gpu")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 11:
+                self.rows.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread is not None:
+                self.thread.join(timeout=5)
+
+    def summary(self, t0: float, t1: float):
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        rows = [r for (t, r) in self.rows if t0 <= t <= t1]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        busy = [r for r in rows if (num(r[10]) or 0) > 0] or rows
+        sm = [num(r[2]) for r in busy if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in busy:
+            for name, v in zip(names, r[6:10]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max((num(r[3]) or 0) for r in busy),
+                "reasons": sorted(reasons), "samples": len(busy),
+                "power_w_max": max((num(r[4]) or 0) for r in busy)}
+
+
+def workload(args, seed_offset=0):
+    import gen
+    n_a, n_b = 1 << args.log2_a, 1 << args.log2_b
+    return gen.large_kv(args.dist, n_a=n_a, n_b=n_b, seed=gen.BASE_SEED + seed_offset)
+
+
+def config_dict(args, n_ranks):
+    return {"workload": "large_kv_merge", "n_a": 1 << args.log2_a, "n_b": 1 << args.log2_b,
+            "key": "uint64", "value": "uint32 (global source index)", "dist": args.dist,
+            "bytes_per_pass": 2 * ((1 << args.log2_a) + (1 << args.log2_b)) * 12,
+            "l2": "no flush: inputs+outputs 8.05 GB per pass >> 129 MB L2",
+            "parallelism": f"replicas x{n_ranks}" if n_ranks > 1 else "single GPU",
+            "plan": args.plan or "auto"}
+
+
+# --------------------------------------------------------------------- oracle
+
+def oracle_rate(a, av, b, bv, target_s=10.0, max_s=30.0):
+    """Time the CPU oracle on the full workload, repeated to ~target_s."""
+    import oracle
+    oracle.build()
+    n = a.size + b.size
+    t0 = time.perf_counter()
+    oracle.merge(a, b, av, bv)
+    t1 = time.perf_counter() - t0
+    reps = 1
+    extra = max(0, min(int(math.ceil(target_s / max(t1, 1e-3))) - 1, int(max_s / max(t1, 1e-3)) - 1))
+    total = t1
+    if extra:
+        t0 = time.perf_counter()
+        for _ in range(extra):
+            oracle.merge(a, b, av, bv)
+        total += time.perf_counter() - t0
+        reps += extra
+    return n * reps / total / 1e9, reps, total
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    a, av, b, bv = workload(args)
+    n = a.size + b.size
+    # Bounded sample: the first m outputs of the merge (a true sub-merge:
+    # A[:a(m)] with B[:m - a(m)]), m sized so the whole run stays within
+    # about two minutes.
+    calib = min(n, 1 << 24)
+    sa, _ = oracle.split(a, b, calib)
+    t0 = time.perf_counter()
+    oracle.merge(a[:sa], b[:calib - sa], av[:sa], bv[:calib - sa])
+    rate = calib / (time.perf_counter() - t0)
+    budget_per_step = 100.0 / max(1, args.steps + args.warmup)
+    m = int(min(n, max(1 << 20, rate * budget_per_step)))
+    sa, _ = oracle.split(a, b, m)
+    A, AV, B, BV = a[:sa], av[:sa], b[:m - sa], bv[:m - sa]
+    for _ in range(args.warmup):
+        oracle.merge(A, B, AV, BV)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.merge(A, B, AV, BV)
+    el = time.perf_counter() - t0
+    value = m * args.steps / el / 1e9
+    sample = f"first {m} outputs of the workload (A[:{sa}] + B[:{m - sa}]), {args.steps} steps"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": config_dict(args, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1406_2628_gb300 as mp
+    from paper_1406_2628_gb300 import build as mpbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0 or not os.path.exists(mpbuild.LIB_PATH):
+        mpbuild.build()
+    if world > 1:
+        dist.barrier()
+    mp.lib()
+    plan = tuple(int(x) for x in args.plan.split(",")) if args.plan else None
+
+    a, av, b, bv = workload(args)
+    n = a.size + b.size
+
+    def dev_t(x, tdt=None):
+        t = torch.from_numpy(x.view(np.int64) if x.dtype == np.uint64 else x.view(np.int32))
+        t = t.to(dev)
+        return t.view(torch.uint64) if x.dtype == np.uint64 else t
+
+    A, AV, B, BV = dev_t(a), dev_t(av), dev_t(b), dev_t(bv)
+    OK = torch.empty(n, dtype=torch.uint64, device=dev)
+    OV = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        if plan is None:
+            mp.mp_merge_pairs(A, AV, B, BV, OK, OV)
+        else:
+            mp.mp_merge_plan(A, B, AV, BV, OK, OV, plan=plan)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    t_load0 = time.time()
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # Per-kernel timing on the same stream: partition alone, merge alone.
+    tile = mp.mp_merge_tile_items(torch.uint64, True, n, plan)
+    splits = mp.mp_merge_path_partition(A, B, tile)
+    torch.cuda.synchronize(dev)
+    reps = max(args.steps, 10)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    for _ in range(reps):
+        mp.mp_merge_path_partition(A, B, tile, out=splits)
+    e1.record(stream)
+    for _ in range(reps):
+        mp.mp_merge_partitioned(A, B, splits, AV, BV, OK, OV, plan=plan)
+    e2.record(stream)
+    torch.cuda.synchronize(dev)
+    t_load1 = time.time()
+    part_ms = e0.elapsed_time(e1) / reps
+    merge_ms = e1.elapsed_time(e2) / reps
+    sampler.stop()
+    clocks = sampler.summary(t_load0, t_load1)
+
+    # End to end through the host-buffer C entry point (pinned host memory).
+    e2e = None
+    if not args.no_e2e:
+        def pin(x, tdt):
+            return torch.from_numpy(x.view(tdt)).pin_memory()
+        hA, hB = pin(a, np.int64).view(torch.uint64), pin(b, np.int64).view(torch.uint64)
+        hAV, hBV = pin(av, np.int32), pin(bv, np.int32)
+        hOK = torch.empty(n, dtype=torch.int64).pin_memory().view(torch.uint64)
+        hOV = torch.empty(n, dtype=torch.int32).pin_memory()
+        mp.mp_merge_pairs_host(hA, hAV, hB, hBV, hOK, hOV)  # warm the pool
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            mp.mp_merge_pairs_host(hA, hAV, hB, hBV, hOK, hOV)
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        if world > 1:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": n * world / e2e_s / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(a.nbytes + av.nbytes + b.nbytes + bv.nbytes),
+               "d2h_bytes_per_step": int(n * 12), "ms_per_step": e2e_s * 1e3,
+               "call": "mp_merge_pairs_host (pinned host buffers, copies in and out inside the call)"}
+        # The result that came back must be the merge of the inputs.
+        chk = hOK.view(torch.int64).numpy().view(np.uint64)
+        if not np.all(chk[1:] >= chk[:-1]):
+            raise RuntimeError("end-to-end result is not sorted")
+
+    peak, peak_kind = measured_peak()
+    alg_bytes = 2 * n * 12
+    achieved = alg_bytes / (merge_ms * 1e-3) / 1e9
+    value = n * world / (ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": config_dict(args, world),
+        "roofline": {"bound": "hbm", "kernel": "merge_tile_kernel", "achieved": achieved,
+                     "peak": peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy)",
+                     "unit": "GB/s", "frac": achieved / peak,
+                     "frac_of_nominal_7900": achieved / NOMINAL_HBM_GBS,
+                     "traffic": recorded_traffic(f"{args.log2_a}_{args.log2_b}_{args.dist}"),
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "kernel_ms": merge_ms, "partition_ms": part_ms,
+                     "step_bytes_per_s_GBs": alg_bytes / (ms * 1e-3) / 1e9},
+        "clocks": clocks,
+        "gpu_launches": 2 * args.steps,
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, reps_o, secs = oracle_rate(a, av, b, bv)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"the full workload merged {reps_o}x by the single-threaded "
+                                          f"oracle ({secs:.1f} s)",
+                                "host_cpus": os.cpu_count()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -40,6 +40,12 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define MP_API __attribute__((visibility("default")))
+#else
+#define MP_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -85,13 +91,13 @@ typedef struct mp_plan {
 #define MP_STAGE_BULK 2
 
 /* Text for a status code (static storage, never NULL). */
-const char* mp_status_string(mp_status status);
+MP_API const char* mp_status_string(mp_status status);
 
 /* Detail of the last error returned on the calling thread ("" if none). */
-const char* mp_last_error(void);
+MP_API const char* mp_last_error(void);
 
 /* Size in bytes of one key of `dtype`, or 0 for an unknown dtype. */
-size_t mp_dtype_size(mp_dtype dtype);
+MP_API size_t mp_dtype_size(mp_dtype dtype);
 
 /*
  * mp_merge_keys -- stable merge of two sorted key arrays (Alg. 1).
@@ -101,7 +107,7 @@ size_t mp_dtype_size(mp_dtype dtype);
  * and a merge kernel (one tile per CTA, Cor. 6).  Scratch: (tiles+1) int64
  * split points from the library pool.
  */
-mp_status mp_merge_keys(mp_dtype dtype, const void* a, int64_t na,
+MP_API mp_status mp_merge_keys(mp_dtype dtype, const void* a, int64_t na,
                         const void* b, int64_t nb, void* out, mp_stream_t stream);
 
 /*
@@ -109,7 +115,7 @@ mp_status mp_merge_keys(mp_dtype dtype, const void* a, int64_t na,
  *   a_vals[i] travels with a_keys[i], b_vals[j] with b_keys[j].  Outputs
  *   out_keys / out_vals (na+nb each) must not overlap any input.
  */
-mp_status mp_merge_pairs(mp_dtype dtype,
+MP_API mp_status mp_merge_pairs(mp_dtype dtype,
                          const void* a_keys, const uint32_t* a_vals, int64_t na,
                          const void* b_keys, const uint32_t* b_vals, int64_t nb,
                          void* out_keys, uint32_t* out_vals, mp_stream_t stream);
@@ -122,7 +128,7 @@ mp_status mp_merge_pairs(mp_dtype dtype,
  *   b_split = d_t - a_split).  a_split: device, ceil((na+nb)/spacing)+1
  *   int64 entries.  spacing >= 1.
  */
-mp_status mp_merge_path_partition(mp_dtype dtype, const void* a, int64_t na,
+MP_API mp_status mp_merge_path_partition(mp_dtype dtype, const void* a, int64_t na,
                                   const void* b, int64_t nb, int64_t spacing,
                                   int64_t* a_split, mp_stream_t stream);
 
@@ -132,20 +138,59 @@ mp_status mp_merge_path_partition(mp_dtype dtype, const void* a, int64_t na,
  * mp_plan_supported() lists the compiled shapes.  Pass a_vals = b_vals =
  * out_vals = NULL to merge keys only.
  */
-mp_status mp_merge_plan(mp_dtype dtype,
+MP_API mp_status mp_merge_plan(mp_dtype dtype,
                         const void* a_keys, const uint32_t* a_vals, int64_t na,
                         const void* b_keys, const uint32_t* b_vals, int64_t nb,
                         void* out_keys, uint32_t* out_vals,
                         const mp_plan* plan, mp_stream_t stream);
 
 /* 1 if (block_threads, items_per_thread, staging) is a compiled merge shape. */
-int mp_plan_supported(const mp_plan* plan);
+MP_API int mp_plan_supported(const mp_plan* plan);
+
+/*
+ * mp_merge_tile_items -- the tile length T (outputs per CTA) that
+ * mp_merge_plan / mp_merge_partitioned use for this dtype, payload choice,
+ * total output length and plan (NULL = automatic).  0 if the plan is not
+ * supported or the dtype unknown.
+ */
+MP_API int64_t mp_merge_tile_items(mp_dtype dtype, int with_values, int64_t total,
+                                   const mp_plan* plan);
+
+/*
+ * mp_merge_partitioned -- the merge kernel of Alg. 1 alone, given the split
+ * points: a_split must hold mp_merge_path_partition(..., spacing = T, ...)
+ * for T = mp_merge_tile_items(dtype, a_vals != NULL, na + nb, plan) and the
+ * same inputs (device, ceil((na+nb)/T)+1 int64).  Arguments otherwise as in
+ * mp_merge_plan.  Lets a caller reuse split points, or time the merge
+ * kernel apart from the partition kernel (the paper times the partition
+ * step separately, Sec. VI).
+ */
+MP_API mp_status mp_merge_partitioned(mp_dtype dtype,
+                                      const void* a_keys, const uint32_t* a_vals, int64_t na,
+                                      const void* b_keys, const uint32_t* b_vals, int64_t nb,
+                                      void* out_keys, uint32_t* out_vals,
+                                      const int64_t* a_split, const mp_plan* plan,
+                                      mp_stream_t stream);
+
+/*
+ * mp_merge_pairs_host -- SYNCHRONOUS end-to-end merge of HOST arrays.
+ *   All six pointers are host memory (page-locked memory gives the best
+ *   copy rate; pageable works).  The library takes device buffers from its
+ *   pool, copies the inputs in, runs mp_merge_pairs on `stream`, copies the
+ *   outputs back and waits for `stream`.  a_vals = b_vals = out_vals = NULL
+ *   merges keys only.  MP_ERR_NO_MEMORY if the device cannot hold the
+ *   inputs and outputs.
+ */
+MP_API mp_status mp_merge_pairs_host(mp_dtype dtype,
+                                     const void* a_keys, const uint32_t* a_vals, int64_t na,
+                                     const void* b_keys, const uint32_t* b_vals, int64_t nb,
+                                     void* out_keys, uint32_t* out_vals, mp_stream_t stream);
 
 /*
  * mp_sort_workspace_bytes -- device workspace that mp_sort needs for n keys
  * (with_values != 0: plus uint32 values).  0 for n <= 1.
  */
-size_t mp_sort_workspace_bytes(mp_dtype dtype, int64_t n, int with_values);
+MP_API size_t mp_sort_workspace_bytes(mp_dtype dtype, int64_t n, int with_values);
 
 /*
  * mp_sort -- stable merge sort in place (Sec. I, Sec. III).
@@ -156,7 +201,7 @@ size_t mp_sort_workspace_bytes(mp_dtype dtype, int64_t n, int with_values);
  *   mp_sort_workspace_bytes(dtype, n, vals != NULL) bytes, 256-byte
  *   aligned, not overlapping keys/vals; its contents are clobbered.
  */
-mp_status mp_sort(mp_dtype dtype, void* keys, uint32_t* vals, int64_t n,
+MP_API mp_status mp_sort(mp_dtype dtype, void* keys, uint32_t* vals, int64_t n,
                   void* workspace, size_t workspace_bytes, mp_stream_t stream);
 
 /*
@@ -173,7 +218,7 @@ mp_status mp_sort(mp_dtype dtype, void* keys, uint32_t* vals, int64_t n,
  * tiles are equal in size whatever the segment lengths and may straddle
  * segments.  plan: NULL = automatic.
  */
-mp_status mp_merge_batched(mp_dtype dtype,
+MP_API mp_status mp_merge_batched(mp_dtype dtype,
                            const void* a, const int64_t* a_off,
                            const void* b, const int64_t* b_off,
                            int64_t nseg, int64_t na_total, int64_t nb_total,
@@ -187,7 +232,7 @@ mp_status mp_merge_batched(mp_dtype dtype,
  * MP_F32, free of NaN.  Returns MP_OK, MP_ERR_NOT_SORTED or MP_ERR_NAN
  * (NaN wins if both).  Waits for `stream`.
  */
-mp_status mp_check_sorted(mp_dtype dtype, const void* keys, int64_t n, mp_stream_t stream);
+MP_API mp_status mp_check_sorted(mp_dtype dtype, const void* keys, int64_t n, mp_stream_t stream);
 
 #ifdef __cplusplus
 }

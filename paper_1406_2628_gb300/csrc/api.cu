@@ -1,0 +1,414 @@
+// api.cu -- the C ABI (include/mp.h): argument checks, scratch memory,
+// dispatch to the kernels, status strings and the sortedness check.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "mp_device.cuh"
+#include "mp_internal.h"
+
+namespace mp {
+
+static thread_local std::string g_last_error;
+
+mp_status fail(mp_status st, const std::string& detail)
+{
+    g_last_error = detail;
+    return st;
+}
+
+mp_status cuda_fail(cudaError_t err, const char* where)
+{
+    std::string d = std::string(where) + ": " + cudaGetErrorName(err) + " (" + cudaGetErrorString(err) + ")";
+    if (err == cudaErrorMemoryAllocation) return fail(MP_ERR_NO_MEMORY, d);
+    return fail(MP_ERR_CUDA, d);
+}
+
+bool key_kind(mp_dtype dtype, KeyKind* k)
+{
+    switch (dtype) {
+    case MP_I32: *k = {4, 0x80000000ull, 0}; return true;
+    case MP_U32: *k = {4, 0, 0}; return true;
+    case MP_F32: *k = {4, 0x80000000ull, 0xFFFFFFFFull}; return true;
+    case MP_U64: *k = {8, 0, 0}; return true;
+    case MP_I64: *k = {8, 0x8000000000000000ull, 0}; return true;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// Scratch: one stream-ordered memory pool per device, owned by the library.
+// Its release threshold keeps freed blocks for reuse, so repeated calls do
+// not go back to the driver.
+// ---------------------------------------------------------------------------
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[64];
+static bool g_pool_made[64];
+
+static mp_status get_pool(cudaMemPool_t* pool)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(MP_ERR_INTERNAL, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool_made[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        e = cudaMemPoolCreate(&g_pools[dev], &props);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemPoolCreate");
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pool_made[dev] = true;
+    }
+    *pool = g_pools[dev];
+    return MP_OK;
+}
+
+mp_status scratch_alloc(void** ptr, size_t bytes, cudaStream_t stream)
+{
+    cudaMemPool_t pool;
+    mp_status st = get_pool(&pool);
+    if (st != MP_OK) return st;
+    cudaError_t e = cudaMallocFromPoolAsync(ptr, bytes < 256 ? 256 : bytes, pool, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
+    return MP_OK;
+}
+
+void scratch_free(void* ptr, cudaStream_t stream)
+{
+    if (ptr) cudaFreeAsync(ptr, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Argument checks.
+// ---------------------------------------------------------------------------
+static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+static bool overlaps(const void* p, size_t pb, const void* q, size_t qb)
+{
+    if (!p || !q || pb == 0 || qb == 0) return false;
+    uintptr_t a = (uintptr_t)p, b = (uintptr_t)q;
+    return a < b + qb && b < a + pb;
+}
+
+static mp_status check_merge_args(const KeyKind& k, const void* a, const uint32_t* av, int64_t na,
+                                  const void* b, const uint32_t* bv, int64_t nb, const void* out,
+                                  const uint32_t* outv, const char* fn)
+{
+    std::string f(fn);
+    if (na < 0 || nb < 0) return fail(MP_ERR_INVALID_ARG, f + ": negative size");
+    if (na > ((int64_t)1 << 46) || nb > ((int64_t)1 << 46)) return fail(MP_ERR_INVALID_ARG, f + ": size too large");
+    const bool vals = av || bv || outv;
+    if (vals && !(av && bv && outv)) return fail(MP_ERR_INVALID_ARG, f + ": give all three value arrays or none");
+    if ((na > 0 && !a) || (nb > 0 && !b) || (na + nb > 0 && !out))
+        return fail(MP_ERR_INVALID_ARG, f + ": NULL key pointer");
+    if (!aligned(a, k.bytes) || !aligned(b, k.bytes) || !aligned(out, k.bytes))
+        return fail(MP_ERR_INVALID_ARG, f + ": key pointer not aligned to the key size");
+    if (vals && (!aligned(av, 4) || !aligned(bv, 4) || !aligned(outv, 4)))
+        return fail(MP_ERR_INVALID_ARG, f + ": value pointer not 4-byte aligned");
+    const size_t ob = (size_t)(na + nb) * k.bytes;
+    if (overlaps(out, ob, a, (size_t)na * k.bytes) || overlaps(out, ob, b, (size_t)nb * k.bytes))
+        return fail(MP_ERR_INVALID_ARG, f + ": output overlaps an input");
+    if (vals) {
+        const size_t ovb = (size_t)(na + nb) * 4;
+        if (overlaps(outv, ovb, av, (size_t)na * 4) || overlaps(outv, ovb, bv, (size_t)nb * 4) ||
+            overlaps(outv, ovb, out, ob) || overlaps(outv, ovb, a, (size_t)na * k.bytes) ||
+            overlaps(outv, ovb, b, (size_t)nb * k.bytes) || overlaps(out, ob, av, (size_t)na * 4) ||
+            overlaps(out, ob, bv, (size_t)nb * 4))
+            return fail(MP_ERR_INVALID_ARG, f + ": value output overlaps another array");
+    }
+    return MP_OK;
+}
+
+static mp_status resolve_shape(const KeyKind& k, bool vals, int64_t total, const mp_plan* plan, Shape* s)
+{
+    *s = default_merge_shape(k.bytes, vals, total);
+    if (plan) {
+        if (plan->reserved != 0) return fail(MP_ERR_INVALID_ARG, "plan.reserved must be 0");
+        if (plan->block_threads) s->nt = plan->block_threads;
+        if (plan->items_per_thread) s->vt = plan->items_per_thread;
+        if (plan->staging) s->staging = plan->staging;
+    }
+    if (!merge_shape_supported(k.bytes, vals, *s))
+        return fail(MP_ERR_INVALID_ARG, "unsupported merge plan (block_threads, items_per_thread, staging)");
+    return MP_OK;
+}
+
+static mp_status merge_impl(mp_dtype dtype, const void* a, const uint32_t* av, int64_t na,
+                            const void* b, const uint32_t* bv, int64_t nb, void* out,
+                            uint32_t* outv, const mp_plan* plan, cudaStream_t stream,
+                            const char* fn, const int64_t* given_splits = nullptr)
+{
+    KeyKind k;
+    if (!key_kind(dtype, &k)) return fail(MP_ERR_UNSUPPORTED_DTYPE, std::string(fn) + ": unknown dtype");
+    mp_status st = check_merge_args(k, a, av, na, b, bv, nb, out, outv, fn);
+    if (st != MP_OK) return st;
+    if (na + nb == 0) return MP_OK;
+    Shape s;
+    st = resolve_shape(k, av != nullptr, na + nb, plan, &s);
+    if (st != MP_OK) return st;
+
+    MergeProblem p;
+    p.kind = k;
+    p.a = a;
+    p.b = b;
+    p.av = av;
+    p.bv = bv;
+    p.out = out;
+    p.outv = outv;
+    p.na = na;
+    p.nb = nb;
+    p.run = 0;
+    if (given_splits) {
+        if (((uintptr_t)given_splits & 7) != 0)
+            return fail(MP_ERR_INVALID_ARG, std::string(fn) + ": a_split not 8-byte aligned");
+        cudaError_t e = launch_merge_tiles(p, s, given_splits, stream);
+        return e == cudaSuccess ? MP_OK : cuda_fail(e, fn);
+    }
+    const int64_t bounds = ceil_div(na + nb, s.tile()) + 1;
+    int64_t* splits = nullptr;
+    st = scratch_alloc((void**)&splits, (size_t)bounds * 8, stream);
+    if (st != MP_OK) return st;
+    cudaError_t e = launch_partition(p, s.tile(), splits, stream);
+    if (e == cudaSuccess) e = launch_merge_tiles(p, s, splits, stream);
+    scratch_free(splits, stream);
+    if (e != cudaSuccess) return cuda_fail(e, fn);
+    return MP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Sortedness / NaN check.
+// ---------------------------------------------------------------------------
+template <class K>
+__global__ void check_sorted_kernel(const K* x, int64_t n, Codec<K> c, bool is_f32, unsigned* flags)
+{
+    unsigned f = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const K v = x[i];
+        if (is_f32 && ((uint32_t)v & 0x7FFFFFFFu) > 0x7F800000u) f |= 2u;
+        if (i + 1 < n && key_enc(v, c) > key_enc(x[i + 1], c)) f |= 1u;
+    }
+    if (f) atomicOr(flags, f);
+}
+
+}  // namespace mp
+
+using namespace mp;
+
+extern "C" {
+
+const char* mp_status_string(mp_status s)
+{
+    switch (s) {
+    case MP_OK: return "MP_OK";
+    case MP_ERR_INVALID_ARG: return "MP_ERR_INVALID_ARG: invalid argument";
+    case MP_ERR_UNSUPPORTED_DTYPE: return "MP_ERR_UNSUPPORTED_DTYPE: unsupported key dtype";
+    case MP_ERR_NOT_SORTED: return "MP_ERR_NOT_SORTED: input is not sorted ascending";
+    case MP_ERR_NAN: return "MP_ERR_NAN: float key is NaN";
+    case MP_ERR_NO_MEMORY: return "MP_ERR_NO_MEMORY: allocation failed";
+    case MP_ERR_BUDGET: return "MP_ERR_BUDGET: request exceeds the memory budget";
+    case MP_ERR_TIMEOUT: return "MP_ERR_TIMEOUT: wait timed out";
+    case MP_ERR_CUDA: return "MP_ERR_CUDA: CUDA runtime error";
+    case MP_ERR_INTERNAL: return "MP_ERR_INTERNAL: internal error";
+    case MP_ERR_NOT_READY: return "MP_ERR_NOT_READY: result not ready";
+    }
+    return "unknown mp_status";
+}
+
+const char* mp_last_error(void) { return g_last_error.c_str(); }
+
+size_t mp_dtype_size(mp_dtype dtype)
+{
+    KeyKind k;
+    return key_kind(dtype, &k) ? (size_t)k.bytes : 0;
+}
+
+mp_status mp_merge_keys(mp_dtype dtype, const void* a, int64_t na, const void* b, int64_t nb,
+                        void* out, mp_stream_t stream)
+{
+    return merge_impl(dtype, a, nullptr, na, b, nullptr, nb, out, nullptr, nullptr,
+                      (cudaStream_t)stream, "mp_merge_keys");
+}
+
+mp_status mp_merge_pairs(mp_dtype dtype, const void* a_keys, const uint32_t* a_vals, int64_t na,
+                         const void* b_keys, const uint32_t* b_vals, int64_t nb, void* out_keys,
+                         uint32_t* out_vals, mp_stream_t stream)
+{
+    if (!a_vals || !b_vals || !out_vals)
+        return fail(MP_ERR_INVALID_ARG, "mp_merge_pairs: value arrays must not be NULL");
+    return merge_impl(dtype, a_keys, a_vals, na, b_keys, b_vals, nb, out_keys, out_vals, nullptr,
+                      (cudaStream_t)stream, "mp_merge_pairs");
+}
+
+mp_status mp_merge_plan(mp_dtype dtype, const void* a_keys, const uint32_t* a_vals, int64_t na,
+                        const void* b_keys, const uint32_t* b_vals, int64_t nb, void* out_keys,
+                        uint32_t* out_vals, const mp_plan* plan, mp_stream_t stream)
+{
+    return merge_impl(dtype, a_keys, a_vals, na, b_keys, b_vals, nb, out_keys, out_vals, plan,
+                      (cudaStream_t)stream, "mp_merge_plan");
+}
+
+int mp_plan_supported(const mp_plan* plan)
+{
+    if (!plan || plan->reserved) return 0;
+    Shape s{plan->block_threads, plan->items_per_thread,
+            plan->staging ? plan->staging : MP_STAGE_VECTOR};
+    return merge_shape_supported(4, false, s) ? 1 : 0;
+}
+
+int64_t mp_merge_tile_items(mp_dtype dtype, int with_values, int64_t total, const mp_plan* plan)
+{
+    KeyKind k;
+    if (!key_kind(dtype, &k)) return 0;
+    Shape s;
+    if (resolve_shape(k, with_values != 0, total, plan, &s) != MP_OK) return 0;
+    return s.tile();
+}
+
+mp_status mp_merge_partitioned(mp_dtype dtype, const void* a_keys, const uint32_t* a_vals, int64_t na,
+                               const void* b_keys, const uint32_t* b_vals, int64_t nb, void* out_keys,
+                               uint32_t* out_vals, const int64_t* a_split, const mp_plan* plan,
+                               mp_stream_t stream)
+{
+    if (na + nb > 0 && !a_split) return fail(MP_ERR_INVALID_ARG, "mp_merge_partitioned: NULL a_split");
+    return merge_impl(dtype, a_keys, a_vals, na, b_keys, b_vals, nb, out_keys, out_vals, plan,
+                      (cudaStream_t)stream, "mp_merge_partitioned", a_split);
+}
+
+mp_status mp_merge_pairs_host(mp_dtype dtype, const void* a_keys, const uint32_t* a_vals, int64_t na,
+                              const void* b_keys, const uint32_t* b_vals, int64_t nb, void* out_keys,
+                              uint32_t* out_vals, mp_stream_t stream)
+{
+    KeyKind k;
+    if (!key_kind(dtype, &k)) return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_merge_pairs_host: unknown dtype");
+    mp_status st = check_merge_args(k, a_keys, a_vals, na, b_keys, b_vals, nb, out_keys, out_vals,
+                                    "mp_merge_pairs_host");
+    if (st != MP_OK) return st;
+    if (na + nb == 0) return MP_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool vals = a_vals != nullptr;
+    const int64_t n = na + nb;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t kb = (size_t)k.bytes;
+    const size_t off_b = al(na * kb), off_o = off_b + al(nb * kb), off_av = off_o + al(n * kb);
+    const size_t off_bv = off_av + (vals ? al(na * 4) : 0), off_ov = off_bv + (vals ? al(nb * 4) : 0);
+    const size_t total = off_ov + (vals ? al(n * 4) : 0);
+    char* d = nullptr;
+    st = scratch_alloc((void**)&d, total, s);
+    if (st != MP_OK) return st;
+    cudaError_t e = cudaSuccess;
+    if (na) e = cudaMemcpyAsync(d, a_keys, na * kb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && nb) e = cudaMemcpyAsync(d + off_b, b_keys, nb * kb, cudaMemcpyHostToDevice, s);
+    if (vals) {
+        if (e == cudaSuccess && na) e = cudaMemcpyAsync(d + off_av, a_vals, na * 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && nb) e = cudaMemcpyAsync(d + off_bv, b_vals, nb * 4, cudaMemcpyHostToDevice, s);
+    }
+    if (e != cudaSuccess) {
+        scratch_free(d, s);
+        return cuda_fail(e, "mp_merge_pairs_host: copy in");
+    }
+    st = merge_impl(dtype, d, vals ? (const uint32_t*)(d + off_av) : nullptr, na, d + off_b,
+                    vals ? (const uint32_t*)(d + off_bv) : nullptr, nb, d + off_o,
+                    vals ? (uint32_t*)(d + off_ov) : nullptr, nullptr, s, "mp_merge_pairs_host");
+    if (st == MP_OK) {
+        e = cudaMemcpyAsync(out_keys, d + off_o, n * kb, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && vals) e = cudaMemcpyAsync(out_vals, d + off_ov, n * 4, cudaMemcpyDeviceToHost, s);
+    }
+    scratch_free(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (st != MP_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "mp_merge_pairs_host");
+    return MP_OK;
+}
+
+mp_status mp_merge_path_partition(mp_dtype dtype, const void* a, int64_t na, const void* b,
+                                  int64_t nb, int64_t spacing, int64_t* a_split, mp_stream_t stream)
+{
+    KeyKind k;
+    if (!key_kind(dtype, &k)) return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_merge_path_partition: unknown dtype");
+    if (na < 0 || nb < 0 || spacing < 1) return fail(MP_ERR_INVALID_ARG, "mp_merge_path_partition: bad size or spacing");
+    if ((na > 0 && !a) || (nb > 0 && !b) || !a_split)
+        return fail(MP_ERR_INVALID_ARG, "mp_merge_path_partition: NULL pointer");
+    if (!aligned(a, k.bytes) || !aligned(b, k.bytes) || !aligned(a_split, 8))
+        return fail(MP_ERR_INVALID_ARG, "mp_merge_path_partition: misaligned pointer");
+    if (na + nb == 0) {
+        cudaError_t e = cudaMemsetAsync(a_split, 0, 8, (cudaStream_t)stream);
+        return e == cudaSuccess ? MP_OK : cuda_fail(e, "mp_merge_path_partition");
+    }
+    MergeProblem p = {};
+    p.kind = k;
+    p.a = a;
+    p.b = b;
+    p.na = na;
+    p.nb = nb;
+    cudaError_t e = launch_partition(p, spacing, a_split, (cudaStream_t)stream);
+    return e == cudaSuccess ? MP_OK : cuda_fail(e, "mp_merge_path_partition");
+}
+
+size_t mp_sort_workspace_bytes(mp_dtype dtype, int64_t n, int with_values)
+{
+    KeyKind k;
+    if (!key_kind(dtype, &k) || n < 0) return 0;
+    return sort_workspace_bytes(k, n, with_values != 0);
+}
+
+mp_status mp_sort(mp_dtype dtype, void* keys, uint32_t* vals, int64_t n, void* workspace,
+                  size_t workspace_bytes, mp_stream_t stream)
+{
+    KeyKind k;
+    if (!key_kind(dtype, &k)) return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_sort: unknown dtype");
+    if (n < 0) return fail(MP_ERR_INVALID_ARG, "mp_sort: negative size");
+    if (n <= 1) return MP_OK;
+    if (!keys) return fail(MP_ERR_INVALID_ARG, "mp_sort: NULL keys");
+    if (!aligned(keys, k.bytes) || (vals && !aligned(vals, 4)))
+        return fail(MP_ERR_INVALID_ARG, "mp_sort: misaligned pointer");
+    const size_t kb = (size_t)n * k.bytes;
+    if (vals && overlaps(keys, kb, vals, (size_t)n * 4))
+        return fail(MP_ERR_INVALID_ARG, "mp_sort: keys and values overlap");
+    if (overlaps(workspace, workspace_bytes, keys, kb) ||
+        (vals && overlaps(workspace, workspace_bytes, vals, (size_t)n * 4)))
+        return fail(MP_ERR_INVALID_ARG, "mp_sort: workspace overlaps the data");
+    return sort_run(k, keys, vals, n, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+mp_status mp_check_sorted(mp_dtype dtype, const void* keys, int64_t n, mp_stream_t stream)
+{
+    KeyKind k;
+    if (!key_kind(dtype, &k)) return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_check_sorted: unknown dtype");
+    if (n < 0 || (n > 0 && !keys)) return fail(MP_ERR_INVALID_ARG, "mp_check_sorted: bad arguments");
+    if (!aligned(keys, k.bytes)) return fail(MP_ERR_INVALID_ARG, "mp_check_sorted: misaligned pointer");
+    if (n == 0) return MP_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned* flags = nullptr;
+    mp_status st = scratch_alloc((void**)&flags, sizeof(unsigned), s);
+    if (st != MP_OK) return st;
+    cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(unsigned), s);
+    const int threads = 256;
+    int64_t blocks = ceil_div(n, threads);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (e == cudaSuccess) {
+        if (k.bytes == 4)
+            check_sorted_kernel<uint32_t><<<(unsigned)blocks, threads, 0, s>>>(
+                (const uint32_t*)keys, n, Codec<uint32_t>{(uint32_t)k.flip, (uint32_t)k.fmask},
+                dtype == MP_F32, flags);
+        else
+            check_sorted_kernel<uint64_t><<<(unsigned)blocks, threads, 0, s>>>(
+                (const uint64_t*)keys, n, Codec<uint64_t>{k.flip, k.fmask}, false, flags);
+        e = cudaGetLastError();
+    }
+    unsigned host_flags = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&host_flags, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    scratch_free(flags, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "mp_check_sorted");
+    if (host_flags & 2u) return fail(MP_ERR_NAN, "mp_check_sorted: NaN key");
+    if (host_flags & 1u) return fail(MP_ERR_NOT_SORTED, "mp_check_sorted: keys out of order");
+    return MP_OK;
+}
+
+}  // extern "C"

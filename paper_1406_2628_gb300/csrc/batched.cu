@@ -1,0 +1,358 @@
+// batched.cu -- many independent merges in one persistent launch.
+//
+// Segment s merges A_s = a[a_off[s]..a_off[s+1]) with B_s = b[b_off[s]..
+// b_off[s+1]) into out at c(s) = a_off[s] + b_off[s].  Concatenated, the
+// segments' outputs form one merge of the concatenated A and B ordered by
+// (segment, key) with ties to A (Cor. 6 applied to the segments), so Merge
+// Path runs over the whole concatenated output: tiles of equal length
+// whatever the segment sizes (Cor. 7), a tile may straddle segments.
+//
+//   partition  for each tile boundary d: the segment s holding output d
+//              (upper bound of d in c(.)), then Alg. 2 inside that segment.
+//   merge      persistent CTAs walk the tiles; each stages its contiguous
+//              A and B windows, each thread finds its segment (upper bound
+//              in c over the tile's few segments) and its split inside the
+//              window, then merges VT outputs, stepping to the next segment
+//              when both sides of the current one are used up.
+#include <algorithm>
+
+#include "mp_device.cuh"
+#include "mp_internal.h"
+#include "mp_tile.cuh"
+
+namespace mp {
+
+template <class K>
+struct BatchArgs {
+    const K* a;
+    const K* b;
+    const uint32_t* av;
+    const uint32_t* bv;
+    K* out;
+    uint32_t* outv;
+    const int64_t* a_off;
+    const int64_t* b_off;
+    int64_t nseg;
+    int64_t na, nb, total;
+    int64_t ntiles;
+    const int64_t* a_split;    // ntiles + 1
+    const int64_t* seg_split;  // ntiles + 1: segment holding output t*T
+    Codec<K> codec;
+};
+
+__device__ __forceinline__ int64_t seg_start(const int64_t* a_off, const int64_t* b_off, int64_t s)
+{
+    return __ldg(a_off + s) + __ldg(b_off + s);
+}
+
+// Largest s in [lo, hi] with c(s) <= d (c(lo) <= d must hold).
+__device__ __forceinline__ int64_t segment_of(const int64_t* a_off, const int64_t* b_off, int64_t lo,
+                                              int64_t hi, int64_t d)
+{
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (seg_start(a_off, b_off, mid) <= d)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <class K>
+__global__ void __launch_bounds__(256) batched_partition_kernel(BatchArgs<K> p, int64_t spacing,
+                                                                int64_t n_bounds, int64_t* a_split,
+                                                                int64_t* seg_split)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_bounds) return;
+    const int64_t d = t * spacing < p.total ? t * spacing : p.total;
+    if (d == p.total) {
+        a_split[t] = p.na;
+        seg_split[t] = p.nseg - 1;
+    } else {
+        const int64_t s = segment_of(p.a_off, p.b_off, 0, p.nseg - 1, d);
+        const int64_t aS = __ldg(p.a_off + s), aE = __ldg(p.a_off + s + 1);
+        const int64_t bS = __ldg(p.b_off + s), bE = __ldg(p.b_off + s + 1);
+        const K* A = p.a + aS;
+        const K* B = p.b + bS;
+        const Codec<K> c = p.codec;
+        const int64_t al = diagonal_search<K>([&](int64_t i) { return key_enc(__ldg(A + i), c); }, aE - aS,
+                                              [&](int64_t i) { return key_enc(__ldg(B + i), c); }, bE - bS,
+                                              d - aS - bS);
+        a_split[t] = aS + al;
+        seg_split[t] = s;
+    }
+    asm volatile("griddepcontrol.launch_dependents;");
+}
+
+template <class K, bool VALS, int NT, int VT>
+__global__ void __launch_bounds__(NT) batched_merge_kernel(BatchArgs<K> p)
+{
+    static_assert(VT % 4 == 0, "VT must be a multiple of 4");
+    constexpr int T = NT * VT;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x;
+    const Codec<K> c = p.codec;
+
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    for (int64_t tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
+        const int64_t d0 = tile * T;
+        const int64_t d1 = d0 + T < p.total ? d0 + T : p.total;
+        // Clamped into the grid and monotone (see merge_tile_kernel).
+        const int64_t a0 = clamp_split(p.a_split[tile], d0, p.na, p.nb);
+        int64_t a1 = clamp_split(p.a_split[tile + 1], d1, p.na, p.nb);
+        a1 = a1 < a0 ? a0 : (a1 > a0 + (d1 - d0) ? a0 + (d1 - d0) : a1);
+        const int64_t b0 = d0 - a0, b1 = d1 - a1;
+        int64_t s0 = p.seg_split[tile], s1 = p.seg_split[tile + 1];
+        s0 = s0 < 0 ? 0 : (s0 > p.nseg - 1 ? p.nseg - 1 : s0);
+        s1 = s1 < s0 ? s0 : (s1 > p.nseg - 1 ? p.nseg - 1 : s1);
+        const int la = (int)(a1 - a0), lb = (int)(b1 - b0);
+        const int L = la + lb;
+
+        const auto v = stage_tile<K, VALS, NT, VT>(smem, p.a + a0, la, p.b + b0, lb,
+                                                   VALS ? p.av + a0 : nullptr,
+                                                   VALS ? p.bv + b0 : nullptr);
+        const int diag = tid * VT < L ? tid * VT : L;
+        uint32_t packed[VT / 2];
+        if (diag < L) {
+            const int64_t dg = d0 + diag;
+            int64_t s = segment_of(p.a_off, p.b_off, s0, s1, dg);
+            const int64_t aS = __ldg(p.a_off + s), aE = __ldg(p.a_off + s + 1);
+            const int64_t bS = __ldg(p.b_off + s), bE = __ldg(p.b_off + s + 1);
+            const int64_t dl = dg - aS - bS;
+            // Alg. 2 inside segment s, restricted to the staged window (the
+            // split at dg lies between the tile's own splits).
+            int64_t lo = dl - (bE - bS);
+            lo = lo > 0 ? lo : 0;
+            lo = lo > a0 - aS ? lo : a0 - aS;
+            lo = lo > dl - (b1 - bS) ? lo : dl - (b1 - bS);
+            int64_t hi = dl < aE - aS ? dl : aE - aS;
+            hi = hi < a1 - aS ? hi : a1 - aS;
+            hi = hi < dl - (b0 - bS) ? hi : dl - (b0 - bS);
+            const K* sAs = v.sA + (aS - a0);  // segment s's A, window-relative
+            const K* sBs = v.sB + (bS - b0);
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (key_enc(sAs[mid], c) > key_enc(sBs[dl - 1 - mid], c))
+                    hi = mid;
+                else
+                    lo = mid + 1;
+            }
+            // Window-relative positions, kept inside the window even for
+            // malformed offsets (no effect on valid input).
+            auto clampi = [](int64_t x, int hi) { return (int)(x < 0 ? 0 : (x > hi ? hi : x)); };
+            int ai = clampi(aS + lo - a0, la);
+            int bi = clampi(bS + dl - lo - b0, lb);
+            int aEnd = clampi((aE < a1 ? aE : a1) - a0, la);
+            int bEnd = clampi((bE < b1 ? bE : b1) - b0, lb);
+            K ka = key_enc(v.sA[ai], c);
+            K kb = key_enc(v.sB[bi], c);
+#pragma unroll
+            for (int i = 0; i < VT; ++i) {
+                uint32_t src = 0;
+                if (diag + i < L) {
+                    // Both sides of segment s used up: step to the next
+                    // segment (skipping empty ones); ai, bi already point at
+                    // its first elements.
+                    while (ai >= aEnd && bi >= bEnd && s + 1 < p.nseg) {
+                        ++s;
+                        const int64_t na1 = __ldg(p.a_off + s + 1), nb1 = __ldg(p.b_off + s + 1);
+                        aEnd = clampi((na1 < a1 ? na1 : a1) - a0, la);
+                        bEnd = clampi((nb1 < b1 ? nb1 : b1) - b0, lb);
+                    }
+                    const bool take_a = ai < aEnd && (bi >= bEnd || !(ka > kb));
+                    src = take_a ? (uint32_t)ai : (uint32_t)(la + bi);
+                    const K* nxt = take_a ? (v.sA + (ai < la ? ai + 1 : la)) : (v.sB + (bi < lb ? bi + 1 : lb));
+                    const K kn = key_enc(*nxt, c);
+                    if (take_a) { ka = kn; ++ai; }
+                    else { kb = kn; ++bi; }
+                }
+                if (i & 1)
+                    packed[i / 2] |= src << 16;
+                else
+                    packed[i / 2] = src;
+            }
+            put_indices<VT>(v.sidx, packed);
+        }
+        __syncthreads();
+        store_tile<K, VALS, NT, VT>(v, p.out + d0, VALS ? p.outv + d0 : nullptr);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+struct BatchedProblem {
+    KeyKind kind;
+    const void* a;
+    const void* b;
+    const int64_t* a_off;
+    const int64_t* b_off;
+    int64_t nseg, na, nb;
+    void* out;
+    const uint32_t* av;
+    const uint32_t* bv;
+    uint32_t* outv;
+};
+
+template <class K>
+static BatchArgs<K> make_batch_args(const BatchedProblem& q, int64_t tile, const int64_t* a_split,
+                                    const int64_t* seg_split)
+{
+    BatchArgs<K> p;
+    p.a = static_cast<const K*>(q.a);
+    p.b = static_cast<const K*>(q.b);
+    p.av = q.av;
+    p.bv = q.bv;
+    p.out = static_cast<K*>(q.out);
+    p.outv = q.outv;
+    p.a_off = q.a_off;
+    p.b_off = q.b_off;
+    p.nseg = q.nseg;
+    p.na = q.na;
+    p.nb = q.nb;
+    p.total = q.na + q.nb;
+    p.ntiles = ceil_div(p.total, tile);
+    p.a_split = a_split;
+    p.seg_split = seg_split;
+    p.codec.flip = (K)q.kind.flip;
+    p.codec.fmask = (K)q.kind.fmask;
+    return p;
+}
+
+template <class K, bool VALS, int NT, int VT>
+static cudaError_t launch_batched_t(const BatchedProblem& q, int64_t* a_split, int64_t* seg_split,
+                                    cudaStream_t stream)
+{
+    using SM = TileSmem<K, VALS, NT, VT>;
+    auto kern = batched_merge_kernel<K, VALS, NT, VT>;
+    static int blocks_per_sm = 0;
+    static int num_sms = 0;
+    if (blocks_per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, NT, SM::bytes);
+        if (e != cudaSuccess) return e;
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    const int64_t T = (int64_t)NT * VT;
+    BatchArgs<K> p = make_batch_args<K>(q, T, a_split, seg_split);
+    const int64_t n_bounds = p.ntiles + 1;
+    batched_partition_kernel<K><<<(unsigned)ceil_div(n_bounds, 256), 256, 0, stream>>>(
+        p, T, n_bounds, a_split, seg_split);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t grid = std::min<int64_t>(p.ntiles, (int64_t)num_sms * blocks_per_sm);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = SM::bytes;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, p);
+}
+
+#define MP_BATCHED_SHAPES(X) X(128, 8) X(256, 8) X(128, 16) X(256, 16)
+
+static bool batched_shape_supported(const Shape& s)
+{
+    if (s.staging != MP_STAGE_VECTOR) return false;
+#define X(NT_, VT_) if (s.nt == NT_ && s.vt == VT_) return true;
+    MP_BATCHED_SHAPES(X)
+#undef X
+    return false;
+}
+
+static cudaError_t launch_batched(const BatchedProblem& q, const Shape& s, int64_t* a_split,
+                                  int64_t* seg_split, cudaStream_t stream)
+{
+    const bool vals = q.av != nullptr;
+#define X(NT_, VT_)                                                                            \
+    if (s.nt == NT_ && s.vt == VT_) {                                                          \
+        if (q.kind.bytes == 4)                                                                 \
+            return vals ? launch_batched_t<uint32_t, true, NT_, VT_>(q, a_split, seg_split, stream)   \
+                        : launch_batched_t<uint32_t, false, NT_, VT_>(q, a_split, seg_split, stream); \
+        return vals ? launch_batched_t<uint64_t, true, NT_, VT_>(q, a_split, seg_split, stream)       \
+                    : launch_batched_t<uint64_t, false, NT_, VT_>(q, a_split, seg_split, stream);     \
+    }
+    MP_BATCHED_SHAPES(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace mp
+
+using namespace mp;
+
+extern "C" mp_status mp_merge_batched(mp_dtype dtype, const void* a, const int64_t* a_off,
+                                      const void* b, const int64_t* b_off, int64_t nseg,
+                                      int64_t na_total, int64_t nb_total, void* out,
+                                      const uint32_t* a_vals, const uint32_t* b_vals,
+                                      uint32_t* out_vals, const mp_plan* plan, mp_stream_t stream)
+{
+    KeyKind k;
+    if (!key_kind(dtype, &k)) return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_merge_batched: unknown dtype");
+    if (nseg < 0 || na_total < 0 || nb_total < 0)
+        return fail(MP_ERR_INVALID_ARG, "mp_merge_batched: negative size");
+    if (nseg == 0 && na_total + nb_total != 0)
+        return fail(MP_ERR_INVALID_ARG, "mp_merge_batched: no segments but nonzero totals");
+    if (nseg > 0 && (!a_off || !b_off))
+        return fail(MP_ERR_INVALID_ARG, "mp_merge_batched: NULL offsets");
+    if (((uintptr_t)a_off & 7) || ((uintptr_t)b_off & 7))
+        return fail(MP_ERR_INVALID_ARG, "mp_merge_batched: offsets not 8-byte aligned");
+    const bool vals = a_vals || b_vals || out_vals;
+    if (vals && !(a_vals && b_vals && out_vals))
+        return fail(MP_ERR_INVALID_ARG, "mp_merge_batched: give all three value arrays or none");
+    if ((na_total > 0 && !a) || (nb_total > 0 && !b) || (na_total + nb_total > 0 && !out))
+        return fail(MP_ERR_INVALID_ARG, "mp_merge_batched: NULL key pointer");
+    if (((uintptr_t)a % k.bytes) || ((uintptr_t)b % k.bytes) || ((uintptr_t)out % k.bytes))
+        return fail(MP_ERR_INVALID_ARG, "mp_merge_batched: key pointer not aligned to the key size");
+    if (vals && (((uintptr_t)a_vals & 3) || ((uintptr_t)b_vals & 3) || ((uintptr_t)out_vals & 3)))
+        return fail(MP_ERR_INVALID_ARG, "mp_merge_batched: value pointer not 4-byte aligned");
+    if (na_total + nb_total == 0) return MP_OK;
+
+    Shape s;
+    s.nt = 256;
+    s.vt = k.bytes == 8 ? 8 : 16;
+    s.staging = MP_STAGE_VECTOR;
+    if (plan) {
+        if (plan->reserved) return fail(MP_ERR_INVALID_ARG, "plan.reserved must be 0");
+        if (plan->block_threads) s.nt = plan->block_threads;
+        if (plan->items_per_thread) s.vt = plan->items_per_thread;
+        if (plan->staging) s.staging = plan->staging;
+    }
+    if (!batched_shape_supported(s)) return fail(MP_ERR_INVALID_ARG, "mp_merge_batched: unsupported plan");
+
+    BatchedProblem q;
+    q.kind = k;
+    q.a = a;
+    q.b = b;
+    q.a_off = a_off;
+    q.b_off = b_off;
+    q.nseg = nseg;
+    q.na = na_total;
+    q.nb = nb_total;
+    q.out = out;
+    q.av = a_vals;
+    q.bv = b_vals;
+    q.outv = out_vals;
+    const int64_t bounds = ceil_div(na_total + nb_total, s.tile()) + 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t* scratch = nullptr;
+    mp_status ms = scratch_alloc((void**)&scratch, (size_t)bounds * 16, st);
+    if (ms != MP_OK) return ms;
+    cudaError_t e = launch_batched(q, s, scratch, scratch + bounds, st);
+    scratch_free(scratch, st);
+    if (e != cudaSuccess) return cuda_fail(e, "mp_merge_batched");
+    return MP_OK;
+}

@@ -1,0 +1,119 @@
+"""C ABI checks that need no GPU: the library builds, loads and exports every
+entry point include/mp.h declares; host-side argument errors and pure host
+queries behave as documented (these return before any CUDA call)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1406_2628_gb300 as mp
+from paper_1406_2628_gb300 import build as mpbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+def declared_symbols():
+    names = []
+    for h in HEADERS:
+        with open(h) as f:
+            text = f.read()
+        names += re.findall(r"^MP_API\s+[\w\s\*]+?\b(mp_\w+)\s*\(", text, flags=re.M)
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    mpbuild.build()
+    return mp.lib()
+
+
+def test_header_declares_entry_points():
+    names = declared_symbols()
+    for required in ["mp_merge_keys", "mp_merge_pairs", "mp_sort", "mp_sort_workspace_bytes",
+                     "mp_merge_batched", "mp_check_sorted", "mp_status_string"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    raw = ctypes.CDLL(mp.LIB_PATH)
+    for name in declared_symbols():
+        assert hasattr(raw, name), f"libmp.so does not export {name}"
+
+
+def test_binding_covers_every_declared_symbol():
+    assert set(declared_symbols()) <= set(mp.exported_symbols())
+
+
+def test_status_strings(lib):
+    for code in range(0, 11):
+        s = mp.mp_status_string(code)
+        assert s and s != "unknown mp_status"
+    assert mp.mp_status_string(99) == "unknown mp_status"
+
+
+def test_dtype_sizes(lib):
+    assert [lib.mp_dtype_size(d) for d in range(5)] == [4, 4, 4, 8, 8]
+    assert lib.mp_dtype_size(7) == 0
+
+
+def test_sort_workspace_bytes(lib):
+    assert mp.mp_sort_workspace_bytes(mp.MP_I32, 0, False) == 0
+    assert mp.mp_sort_workspace_bytes(mp.MP_I32, 1, False) == 0
+    n = 1 << 20
+    k = mp.mp_sort_workspace_bytes(mp.MP_I32, n, False)
+    kv = mp.mp_sort_workspace_bytes(mp.MP_I32, n, True)
+    assert k >= n * 4 and kv >= k + n * 4
+    assert mp.mp_sort_workspace_bytes(mp.MP_U64, n, False) >= n * 8
+    assert mp.mp_sort_workspace_bytes(9, n, False) == 0
+
+
+def test_host_argument_errors(lib):
+    # Negative sizes and NULL pointers are rejected on the host, before any
+    # CUDA call, with a detail message.
+    st = lib.mp_merge_keys(mp.MP_I32, None, -1, None, 0, None, None)
+    assert st == mp.MP_ERR_INVALID_ARG
+    assert "negative" in mp.mp_last_error()
+    st = lib.mp_merge_keys(mp.MP_I32, None, 5, None, 0, None, None)
+    assert st == mp.MP_ERR_INVALID_ARG
+    st = lib.mp_merge_keys(17, None, 0, None, 0, None, None)
+    assert st == mp.MP_ERR_UNSUPPORTED_DTYPE
+    # Misaligned key pointer.
+    st = lib.mp_merge_keys(mp.MP_U64, 0x1004, 1, 0x2000, 1, 0x3000, None)
+    assert st == mp.MP_ERR_INVALID_ARG and "aligned" in mp.mp_last_error()
+    # Output overlapping an input.
+    st = lib.mp_merge_keys(mp.MP_I32, 0x10000, 100, 0x20000, 100, 0x10100, None)
+    assert st == mp.MP_ERR_INVALID_ARG and "overlap" in mp.mp_last_error()
+    # Empty merge is a no-op.
+    assert lib.mp_merge_keys(mp.MP_I32, None, 0, None, 0, None, None) == mp.MP_OK
+    # Pairs need all value arrays.
+    st = lib.mp_merge_pairs(mp.MP_I32, 0x1000, None, 1, 0x2000, None, 1, 0x3000, None, None)
+    assert st == mp.MP_ERR_INVALID_ARG
+    # Sort: workspace too small / misaligned; n <= 1 is a no-op.
+    assert lib.mp_sort(mp.MP_I32, None, None, 1, None, 0, None) == mp.MP_OK
+    st = lib.mp_sort(mp.MP_I32, 0x100000, None, 1 << 20, 0x8000000, 16, None)
+    assert st == mp.MP_ERR_INVALID_ARG and "workspace" in mp.mp_last_error()
+    # Batched: inconsistent totals, bad plan.
+    st = lib.mp_merge_batched(mp.MP_I32, None, None, None, None, 0, 5, 0, None, None, None, None,
+                              None, None)
+    assert st == mp.MP_ERR_INVALID_ARG
+    bad = mp.mp_plan(100, 3, 0, 0)
+    st = lib.mp_merge_batched(mp.MP_I32, 0x1000, 0x2000, 0x3000, 0x4000, 1, 1, 1, 0x5000, None,
+                              None, None, ctypes.byref(bad), None)
+    assert st == mp.MP_ERR_INVALID_ARG and "plan" in mp.mp_last_error()
+
+
+def test_plan_supported(lib):
+    assert mp.mp_plan_supported((256, 8))
+    assert mp.mp_plan_supported((128, 16, mp.MP_STAGE_VECTOR))
+    assert not mp.mp_plan_supported((100, 3))
+    assert not mp.mp_plan_supported((256, 7))
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    monkeypatch.setattr(mp, "_lib", None)
+    monkeypatch.setattr(mp, "LIB_PATH", str(tmp_path / "libmp.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        mp.lib()
