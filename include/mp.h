@@ -20,7 +20,8 @@
  *    current device.  The caller owns all memory it passes in; the library
  *    never frees it.  Key pointers must be aligned to the key size, value
  *    pointers to 4 bytes.  Outputs must not overlap inputs unless stated.
- *  - Values (payloads) are always uint32 and move with their keys.
+ *  - Values (payloads) are always uint32 and move with their keys.  A value
+ *    pointer may be NULL when its array has zero elements.
  *  - Sizes are int64 element counts (arrays may exceed 2^31 elements).
  *  - Streams: work is enqueued on `stream` (NULL = the legacy default stream)
  *    and the call returns without waiting, unless its comment says it
@@ -135,8 +136,9 @@ MP_API mp_status mp_merge_path_partition(mp_dtype dtype, const void* a, int64_t 
 /*
  * mp_merge_plan -- mp_merge_keys / mp_merge_pairs with an explicit tile
  * plan (NULL = automatic).  An unsupported plan returns MP_ERR_INVALID_ARG;
- * mp_plan_supported() lists the compiled shapes.  Pass a_vals = b_vals =
- * out_vals = NULL to merge keys only.
+ * mp_plan_supported() lists the compiled shapes.  Values are merged when any
+ * of a_vals, b_vals, out_vals is non-NULL; pass all three NULL to merge keys
+ * only.
  */
 MP_API mp_status mp_merge_plan(mp_dtype dtype,
                         const void* a_keys, const uint32_t* a_vals, int64_t na,

@@ -98,13 +98,13 @@ static bool overlaps(const void* p, size_t pb, const void* q, size_t qb)
 
 static mp_status check_merge_args(const KeyKind& k, const void* a, const uint32_t* av, int64_t na,
                                   const void* b, const uint32_t* bv, int64_t nb, const void* out,
-                                  const uint32_t* outv, const char* fn)
+                                  const uint32_t* outv, bool vals, const char* fn)
 {
     std::string f(fn);
     if (na < 0 || nb < 0) return fail(MP_ERR_INVALID_ARG, f + ": negative size");
     if (na > ((int64_t)1 << 46) || nb > ((int64_t)1 << 46)) return fail(MP_ERR_INVALID_ARG, f + ": size too large");
-    const bool vals = av || bv || outv;
-    if (vals && !(av && bv && outv)) return fail(MP_ERR_INVALID_ARG, f + ": give all three value arrays or none");
+    if (vals && ((na > 0 && !av) || (nb > 0 && !bv) || (na + nb > 0 && !outv)))
+        return fail(MP_ERR_INVALID_ARG, f + ": NULL value array for a non-empty side");
     if ((na > 0 && !a) || (nb > 0 && !b) || (na + nb > 0 && !out))
         return fail(MP_ERR_INVALID_ARG, f + ": NULL key pointer");
     if (!aligned(a, k.bytes) || !aligned(b, k.bytes) || !aligned(out, k.bytes))
@@ -141,20 +141,21 @@ static mp_status resolve_shape(const KeyKind& k, bool vals, int64_t total, const
 
 static mp_status merge_impl(mp_dtype dtype, const void* a, const uint32_t* av, int64_t na,
                             const void* b, const uint32_t* bv, int64_t nb, void* out,
-                            uint32_t* outv, const mp_plan* plan, cudaStream_t stream,
+                            uint32_t* outv, bool vals, const mp_plan* plan, cudaStream_t stream,
                             const char* fn, const int64_t* given_splits = nullptr)
 {
     KeyKind k;
     if (!key_kind(dtype, &k)) return fail(MP_ERR_UNSUPPORTED_DTYPE, std::string(fn) + ": unknown dtype");
-    mp_status st = check_merge_args(k, a, av, na, b, bv, nb, out, outv, fn);
+    mp_status st = check_merge_args(k, a, av, na, b, bv, nb, out, outv, vals, fn);
     if (st != MP_OK) return st;
     if (na + nb == 0) return MP_OK;
     Shape s;
-    st = resolve_shape(k, av != nullptr, na + nb, plan, &s);
+    st = resolve_shape(k, vals, na + nb, plan, &s);
     if (st != MP_OK) return st;
 
     MergeProblem p;
     p.kind = k;
+    p.vals = vals;
     p.a = a;
     p.b = b;
     p.av = av;
@@ -231,7 +232,7 @@ size_t mp_dtype_size(mp_dtype dtype)
 mp_status mp_merge_keys(mp_dtype dtype, const void* a, int64_t na, const void* b, int64_t nb,
                         void* out, mp_stream_t stream)
 {
-    return merge_impl(dtype, a, nullptr, na, b, nullptr, nb, out, nullptr, nullptr,
+    return merge_impl(dtype, a, nullptr, na, b, nullptr, nb, out, nullptr, false, nullptr,
                       (cudaStream_t)stream, "mp_merge_keys");
 }
 
@@ -239,9 +240,7 @@ mp_status mp_merge_pairs(mp_dtype dtype, const void* a_keys, const uint32_t* a_v
                          const void* b_keys, const uint32_t* b_vals, int64_t nb, void* out_keys,
                          uint32_t* out_vals, mp_stream_t stream)
 {
-    if (!a_vals || !b_vals || !out_vals)
-        return fail(MP_ERR_INVALID_ARG, "mp_merge_pairs: value arrays must not be NULL");
-    return merge_impl(dtype, a_keys, a_vals, na, b_keys, b_vals, nb, out_keys, out_vals, nullptr,
+    return merge_impl(dtype, a_keys, a_vals, na, b_keys, b_vals, nb, out_keys, out_vals, true, nullptr,
                       (cudaStream_t)stream, "mp_merge_pairs");
 }
 
@@ -249,7 +248,8 @@ mp_status mp_merge_plan(mp_dtype dtype, const void* a_keys, const uint32_t* a_va
                         const void* b_keys, const uint32_t* b_vals, int64_t nb, void* out_keys,
                         uint32_t* out_vals, const mp_plan* plan, mp_stream_t stream)
 {
-    return merge_impl(dtype, a_keys, a_vals, na, b_keys, b_vals, nb, out_keys, out_vals, plan,
+    const bool vals = a_vals || b_vals || out_vals;
+    return merge_impl(dtype, a_keys, a_vals, na, b_keys, b_vals, nb, out_keys, out_vals, vals, plan,
                       (cudaStream_t)stream, "mp_merge_plan");
 }
 
@@ -276,7 +276,8 @@ mp_status mp_merge_partitioned(mp_dtype dtype, const void* a_keys, const uint32_
                                mp_stream_t stream)
 {
     if (na + nb > 0 && !a_split) return fail(MP_ERR_INVALID_ARG, "mp_merge_partitioned: NULL a_split");
-    return merge_impl(dtype, a_keys, a_vals, na, b_keys, b_vals, nb, out_keys, out_vals, plan,
+    const bool vals = a_vals || b_vals || out_vals;
+    return merge_impl(dtype, a_keys, a_vals, na, b_keys, b_vals, nb, out_keys, out_vals, vals, plan,
                       (cudaStream_t)stream, "mp_merge_partitioned", a_split);
 }
 
@@ -286,12 +287,12 @@ mp_status mp_merge_pairs_host(mp_dtype dtype, const void* a_keys, const uint32_t
 {
     KeyKind k;
     if (!key_kind(dtype, &k)) return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_merge_pairs_host: unknown dtype");
+    const bool vals = a_vals || b_vals || out_vals;
     mp_status st = check_merge_args(k, a_keys, a_vals, na, b_keys, b_vals, nb, out_keys, out_vals,
-                                    "mp_merge_pairs_host");
+                                    vals, "mp_merge_pairs_host");
     if (st != MP_OK) return st;
     if (na + nb == 0) return MP_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    const bool vals = a_vals != nullptr;
     const int64_t n = na + nb;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t kb = (size_t)k.bytes;
@@ -314,7 +315,7 @@ mp_status mp_merge_pairs_host(mp_dtype dtype, const void* a_keys, const uint32_t
     }
     st = merge_impl(dtype, d, vals ? (const uint32_t*)(d + off_av) : nullptr, na, d + off_b,
                     vals ? (const uint32_t*)(d + off_bv) : nullptr, nb, d + off_o,
-                    vals ? (uint32_t*)(d + off_ov) : nullptr, nullptr, s, "mp_merge_pairs_host");
+                    vals ? (uint32_t*)(d + off_ov) : nullptr, vals, nullptr, s, "mp_merge_pairs_host");
     if (st == MP_OK) {
         e = cudaMemcpyAsync(out_keys, d + off_o, n * kb, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && vals) e = cudaMemcpyAsync(out_vals, d + off_ov, n * 4, cudaMemcpyDeviceToHost, s);
@@ -342,6 +343,7 @@ mp_status mp_merge_path_partition(mp_dtype dtype, const void* a, int64_t na, con
     }
     MergeProblem p = {};
     p.kind = k;
+    p.vals = false;
     p.a = a;
     p.b = b;
     p.na = na;

@@ -192,6 +192,7 @@ struct BatchedProblem {
     const int64_t* b_off;
     int64_t nseg, na, nb;
     void* out;
+    bool vals;
     const uint32_t* av;
     const uint32_t* bv;
     uint32_t* outv;
@@ -276,7 +277,7 @@ static bool batched_shape_supported(const Shape& s)
 static cudaError_t launch_batched(const BatchedProblem& q, const Shape& s, int64_t* a_split,
                                   int64_t* seg_split, cudaStream_t stream)
 {
-    const bool vals = q.av != nullptr;
+    const bool vals = q.vals;
 #define X(NT_, VT_)                                                                            \
     if (s.nt == NT_ && s.vt == VT_) {                                                          \
         if (q.kind.bytes == 4)                                                                 \
@@ -311,8 +312,8 @@ extern "C" mp_status mp_merge_batched(mp_dtype dtype, const void* a, const int64
     if (((uintptr_t)a_off & 7) || ((uintptr_t)b_off & 7))
         return fail(MP_ERR_INVALID_ARG, "mp_merge_batched: offsets not 8-byte aligned");
     const bool vals = a_vals || b_vals || out_vals;
-    if (vals && !(a_vals && b_vals && out_vals))
-        return fail(MP_ERR_INVALID_ARG, "mp_merge_batched: give all three value arrays or none");
+    if (vals && ((na_total > 0 && !a_vals) || (nb_total > 0 && !b_vals) || (na_total + nb_total > 0 && !out_vals)))
+        return fail(MP_ERR_INVALID_ARG, "mp_merge_batched: NULL value array for a non-empty side");
     if ((na_total > 0 && !a) || (nb_total > 0 && !b) || (na_total + nb_total > 0 && !out))
         return fail(MP_ERR_INVALID_ARG, "mp_merge_batched: NULL key pointer");
     if (((uintptr_t)a % k.bytes) || ((uintptr_t)b % k.bytes) || ((uintptr_t)out % k.bytes))
@@ -343,6 +344,7 @@ extern "C" mp_status mp_merge_batched(mp_dtype dtype, const void* a, const int64
     q.na = na_total;
     q.nb = nb_total;
     q.out = out;
+    q.vals = vals;
     q.av = a_vals;
     q.bv = b_vals;
     q.outv = out_vals;

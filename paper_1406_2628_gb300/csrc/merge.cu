@@ -222,7 +222,7 @@ Shape default_merge_shape(int key_bytes, bool with_values, int64_t total)
 cudaError_t launch_merge_tiles(const MergeProblem& p, const Shape& s, const int64_t* a_split,
                                cudaStream_t stream)
 {
-    const bool vals = p.av != nullptr;
+    const bool vals = p.vals;
 #define X(NT_, VT_)                                                                            \
     if (s.nt == NT_ && s.vt == VT_) {                                                          \
         if (p.kind.bytes == 4)                                                                 \

@@ -34,7 +34,8 @@ struct MergeProblem {
     KeyKind kind;
     const void* a;
     const void* b;
-    const uint32_t* av;  // NULL: keys only
+    bool vals;           // move uint32 values with the keys
+    const uint32_t* av;  // may be NULL when its side is empty
     const uint32_t* bv;
     void* out;
     uint32_t* outv;

@@ -211,6 +211,7 @@ mp_status sort_run(const KeyKind& kind, void* keys, uint32_t* vals, int64_t n, v
     for (int p = 0; p < passes; ++p) {
         MergeProblem mp;
         mp.kind = kind;
+        mp.vals = with_vals;
         mp.a = cur;
         mp.b = cur;
         mp.av = curv;
