@@ -198,3 +198,37 @@ def batched(n_seg: int = 16384, log2_max: float = 18.0, seed: int = BASE_SEED,
     av = np.arange(a.size, dtype=np.uint32)
     bv = np.arange(a.size, a.size + b.size, dtype=np.uint64).astype(np.uint32)
     return a, a_off, b, b_off, av, bv
+
+
+# --------------------------------------------------------------------------
+# The device generator's definition (mp_generate / MP_SRC_GENERATE), restated
+# in numpy so that generated requests can be checked on the host.
+# --------------------------------------------------------------------------
+
+def device_generated(n: int, seed: int, stream: int, sorted_: bool, key_bits: int = 32,
+                     val_base: int = 0):
+    """keys (uint32 or uint64) and uint32 values val_base + i."""
+    x = splitmix64(seed, stream, n)
+    if sorted_:
+        if key_bits == 32:
+            stride = max(1, (1 << 32) // max(n, 1))
+        else:
+            stride = max(1, ((1 << 64) - 1) // max(n, 1))
+        with np.errstate(over="ignore"):
+            k = np.arange(n, dtype=np.uint64) * np.uint64(stride) + x % np.uint64(stride)
+    else:
+        k = x if key_bits == 64 else (x >> np.uint64(32))
+    keys = k.astype(np.uint32) if key_bits == 32 else k
+    vals = (np.arange(n, dtype=np.uint64) + np.uint64(val_base)).astype(np.uint32)
+    return keys, vals
+
+
+def serving_request(op: str, na: int, nb: int, seed: int, key_bits: int = 32):
+    """Inputs of a generated queue request: merge -> (a, av, b, bv) with
+    streams 1 and 2 (B's values continue after A's); sort -> (keys, vals)
+    with stream 3."""
+    if op == "merge":
+        a, av = device_generated(na, seed, 1, True, key_bits, 0)
+        b, bv = device_generated(nb, seed, 2, True, key_bits, na)
+        return a, av, b, bv
+    return device_generated(na, seed, 3, False, key_bits, 0)

@@ -229,12 +229,217 @@ MP_API mp_status mp_merge_batched(mp_dtype dtype,
                            uint32_t* out_vals,
                            const mp_plan* plan, mp_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Autotuning of tile shapes.
+ * ------------------------------------------------------------------------ */
+
+/*
+ * mp_autotune_merge -- SYNCHRONOUS.  Times every compiled tile shape of the
+ * merge kernels on the given problem (arguments as in mp_merge_plan; the
+ * output arrays are overwritten with the merge), each the fastest of `reps`
+ * partition + merge runs under CUDA events, and records the fastest for
+ * this device, key width, payload choice and size class floor(log2(na+nb)).
+ * Later calls with automatic plans (plan NULL or zero fields) in that class
+ * use it.  *best (if not NULL) receives it.
+ */
+MP_API mp_status mp_autotune_merge(mp_dtype dtype,
+                                   const void* a_keys, const uint32_t* a_vals, int64_t na,
+                                   const void* b_keys, const uint32_t* b_vals, int64_t nb,
+                                   void* out_keys, uint32_t* out_vals, int reps, mp_plan* best,
+                                   mp_stream_t stream);
+
+/* As mp_autotune_merge, for mp_merge_batched (arguments as there). */
+MP_API mp_status mp_autotune_batched(mp_dtype dtype,
+                                     const void* a, const int64_t* a_off,
+                                     const void* b, const int64_t* b_off,
+                                     int64_t nseg, int64_t na_total, int64_t nb_total, void* out,
+                                     const uint32_t* a_vals, const uint32_t* b_vals,
+                                     uint32_t* out_vals, int reps, mp_plan* best,
+                                     mp_stream_t stream);
+
+/* Save / load / clear the tuned-shape table (text, one entry per line).  If
+ * the environment variable MP_TUNE_CACHE names a file, it is loaded on first
+ * use of an automatic plan. */
+MP_API mp_status mp_tune_save(const char* path);
+MP_API mp_status mp_tune_load(const char* path);
+MP_API void mp_tune_clear(void);
+
+/* ------------------------------------------------------------------------
+ * CUDA graphs: capture a merge once, replay it with one launch.  The graph
+ * bakes in every pointer and size given at creation (the caller keeps those
+ * buffers alive and may change their contents between replays) and owns its
+ * scratch, so a replay allocates nothing.
+ * ------------------------------------------------------------------------ */
+typedef struct mp_graph mp_graph;
+
+/* Arguments as mp_merge_plan (values merged when any value pointer is set). */
+MP_API mp_status mp_graph_merge_create(mp_dtype dtype,
+                                       const void* a_keys, const uint32_t* a_vals, int64_t na,
+                                       const void* b_keys, const uint32_t* b_vals, int64_t nb,
+                                       void* out_keys, uint32_t* out_vals, const mp_plan* plan,
+                                       mp_graph** graph);
+
+/* Arguments as mp_merge_batched (the offsets' contents are read at replay). */
+MP_API mp_status mp_graph_batched_create(mp_dtype dtype,
+                                         const void* a, const int64_t* a_off,
+                                         const void* b, const int64_t* b_off,
+                                         int64_t nseg, int64_t na_total, int64_t nb_total,
+                                         void* out, const uint32_t* a_vals,
+                                         const uint32_t* b_vals, uint32_t* out_vals,
+                                         const mp_plan* plan, mp_graph** graph);
+
+/* Enqueue one replay on `stream`. */
+MP_API mp_status mp_graph_launch(mp_graph* graph, mp_stream_t stream);
+
+/* Waits for the device, then frees the graph and its scratch. */
+MP_API mp_status mp_graph_destroy(mp_graph* graph);
+
+/* One problem of mp_merge_grouped. */
+typedef struct mp_merge_desc {
+    int32_t dtype;    /* mp_dtype of this problem's keys */
+    int32_t reserved; /* must be 0 */
+    const void* a_keys;
+    const uint32_t* a_vals; /* NULL if keys only (or na == 0) */
+    int64_t na;
+    const void* b_keys;
+    const uint32_t* b_vals;
+    int64_t nb;
+    void* out_keys; /* na + nb keys */
+    uint32_t* out_vals;
+} mp_merge_desc;
+
+/*
+ * mp_merge_grouped -- nprob independent stable merges, each with its own
+ * pointers, in one partition launch and one merge launch (Alg. 1 per
+ * problem; every problem is cut into equal tiles, Cor. 7, and the tiles of
+ * all problems share one grid).  descs: HOST array of nprob descriptors
+ * (copied before the call returns); every problem's arrays follow the
+ * rules of mp_merge_pairs (device memory, sorted, no overlap).  All dtypes
+ * in one call must have the same key width; with_values != 0 moves values
+ * for every problem.  Scratch (descriptor table + split points) comes from
+ * the library pool.
+ */
+MP_API mp_status mp_merge_grouped(const mp_merge_desc* descs, int64_t nprob, int with_values,
+                                  mp_stream_t stream);
+
 /*
  * mp_check_sorted -- SYNCHRONOUS check that keys[0..n) is ascending and, for
  * MP_F32, free of NaN.  Returns MP_OK, MP_ERR_NOT_SORTED or MP_ERR_NAN
  * (NaN wins if both).  Waits for `stream`.
  */
 MP_API mp_status mp_check_sorted(mp_dtype dtype, const void* keys, int64_t n, mp_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Request queue: continuous batching of merge and sort requests.
+ *
+ * Requests are admitted in arrival order while the queue's device-memory
+ * budget and slot limit allow; an admitted request keeps its buffers on the
+ * device until it completes.  A scheduler thread runs steps; each step
+ * advances every admitted request by one stage in one grouped launch per
+ * key width and payload choice: a merge is one stage (Alg. 1), a sort is a
+ * block-sort stage plus one stage per Merge Path pass (Sec. I, Sec. III), so
+ * requests of any size share the GPU and later arrivals join at the next
+ * step.  Results are written to the caller's buffers; memory and budget
+ * are released as soon as a request's last stage has run.  The paper has
+ * no serving layer; this is a systems pattern around its merge.
+ * ------------------------------------------------------------------------ */
+typedef struct mp_queue mp_queue;
+
+typedef enum mp_op { MP_OP_MERGE = 0, MP_OP_SORT = 1 } mp_op;
+
+/* Where a request's inputs come from. */
+typedef enum mp_source {
+    MP_SRC_HOST = 0,     /* host arrays, copied in at admission */
+    MP_SRC_DEVICE = 1,   /* device arrays, copied in at admission */
+    MP_SRC_GENERATE = 2  /* synthetic, generated on the device from `seed` (see mp_generate) */
+} mp_source;
+
+/* Where its result goes. */
+typedef enum mp_sink {
+    MP_SINK_HOST = 0,    /* out_keys/out_vals are host arrays */
+    MP_SINK_DEVICE = 1,  /* out_keys/out_vals are device arrays */
+    MP_SINK_DISCARD = 2  /* result dropped (load generation) */
+} mp_sink;
+
+typedef struct mp_request {
+    int32_t op;          /* mp_op */
+    int32_t dtype;       /* mp_dtype of the keys */
+    int32_t with_values; /* nonzero: uint32 values travel with the keys */
+    int32_t source;      /* mp_source */
+    int32_t sink;        /* mp_sink */
+    int32_t reserved;    /* 0 */
+    const void* a_keys;  /* merge: A (sorted); sort: the keys to sort */
+    const uint32_t* a_vals;
+    int64_t na;          /* merge: |A|; sort: n */
+    const void* b_keys;  /* merge: B (sorted); sort: unused */
+    const uint32_t* b_vals;
+    int64_t nb;          /* merge: |B|; sort: must be 0 */
+    uint64_t seed;       /* MP_SRC_GENERATE only */
+    void* out_keys;      /* na (+ nb) keys, unless MP_SINK_DISCARD */
+    uint32_t* out_vals;
+} mp_request;
+
+typedef struct mp_result {
+    mp_status status;
+    int32_t op;
+    int64_t n;           /* number of output elements */
+    double t_submit;     /* mp_clock_seconds() at submission */
+    double t_admit;      /* ... when admitted (buffers allocated, inputs enqueued) */
+    double t_done;       /* ... when the scheduler saw the result copied out */
+} mp_result;
+
+typedef struct mp_queue_stats {
+    uint64_t submitted, completed, failed;
+    uint64_t steps;       /* scheduler steps run */
+    uint64_t launches;    /* kernel launches made by steps */
+    uint64_t peak_bytes;  /* highest device bytes held by admitted requests */
+    uint64_t waiting, active, bytes_in_use;
+} mp_queue_stats;
+
+/* Monotonic host clock (seconds) used for the timestamps in mp_result. */
+MP_API double mp_clock_seconds(void);
+
+/*
+ * mp_queue_create -- a queue on the current device.  budget_bytes: device
+ * memory that admitted requests may hold together (a request needs about
+ * 2 x its output bytes, inputs included); max_active: admitted requests at
+ * once.  The queue owns a scheduler thread, two streams and a memory pool.
+ */
+MP_API mp_status mp_queue_create(size_t budget_bytes, int max_active, mp_queue** q);
+
+/*
+ * mp_queue_submit -- non-blocking.  Copies *r; the caller's input arrays
+ * must stay valid until the request is admitted and its output arrays until
+ * mp_queue_wait reports it done.  MP_ERR_BUDGET if the request alone needs
+ * more than the budget; argument errors as for mp_merge_pairs / mp_sort.
+ * Generated inputs (MP_SRC_GENERATE) support MP_U32 and MP_U64 keys.
+ */
+MP_API mp_status mp_queue_submit(mp_queue* q, const mp_request* r, uint64_t* ticket);
+
+/*
+ * mp_queue_wait -- wait for a request: timeout_ns < 0 waits without limit,
+ * 0 polls (MP_ERR_NOT_READY if not done), > 0 waits at most that long
+ * (MP_ERR_TIMEOUT).  On MP_OK, *res holds the request's own status and
+ * timestamps and the ticket is retired.
+ */
+MP_API mp_status mp_queue_wait(mp_queue* q, uint64_t ticket, int64_t timeout_ns, mp_result* res);
+
+MP_API mp_status mp_queue_get_stats(mp_queue* q, mp_queue_stats* stats);
+
+/* Drains all submitted requests, stops the scheduler and frees the queue. */
+MP_API mp_status mp_queue_destroy(mp_queue* q);
+
+/*
+ * mp_generate -- synthetic keys on the device (the generator behind
+ * MP_SRC_GENERATE).  SplitMix64 (Steele, Lea, Flood 2014) as a counter-based
+ * generator: x_i = mix(seed ^ (stream_id * 0xD1B54A32D192ED03) +
+ * (i + 1) * 0x9E3779B97F4A7C15).  sorted != 0: key_i = i * stride +
+ * (x_i mod stride) with stride = floor(2^w / n) (strictly increasing);
+ * sorted == 0: key_i = top w bits of x_i (w = key bits).  vals (may be NULL)
+ * get val_base + i.  MP_U32 or MP_U64 keys.
+ */
+MP_API mp_status mp_generate(mp_dtype dtype, void* keys, uint32_t* vals, int64_t n, uint64_t seed,
+                             uint64_t stream_id, int sorted, uint32_t val_base, mp_stream_t stream);
 
 #ifdef __cplusplus
 }

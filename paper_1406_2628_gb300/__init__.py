@@ -36,6 +36,11 @@ MP_ERR_NOT_READY = 10
 # mp_dtype
 MP_I32, MP_U32, MP_F32, MP_U64, MP_I64 = 0, 1, 2, 3, 4
 
+# request queue enums
+MP_OP_MERGE, MP_OP_SORT = 0, 1
+MP_SRC_HOST, MP_SRC_DEVICE, MP_SRC_GENERATE = 0, 1, 2
+MP_SINK_HOST, MP_SINK_DEVICE, MP_SINK_DISCARD = 0, 1, 2
+
 MP_STAGE_AUTO, MP_STAGE_VECTOR, MP_STAGE_BULK = 0, 1, 2
 
 _TORCH_DTYPE = {
@@ -51,6 +56,31 @@ class MPError(RuntimeError):
     def __init__(self, status: int, detail: str):
         super().__init__(f"{detail} [status {status}]")
         self.status = status
+
+
+class mp_merge_desc(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("a_keys", ctypes.c_void_p), ("a_vals", ctypes.c_void_p), ("na", ctypes.c_int64),
+                ("b_keys", ctypes.c_void_p), ("b_vals", ctypes.c_void_p), ("nb", ctypes.c_int64),
+                ("out_keys", ctypes.c_void_p), ("out_vals", ctypes.c_void_p)]
+
+
+class mp_request(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("dtype", ctypes.c_int32), ("with_values", ctypes.c_int32),
+                ("source", ctypes.c_int32), ("sink", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("a_keys", ctypes.c_void_p), ("a_vals", ctypes.c_void_p), ("na", ctypes.c_int64),
+                ("b_keys", ctypes.c_void_p), ("b_vals", ctypes.c_void_p), ("nb", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("out_keys", ctypes.c_void_p), ("out_vals", ctypes.c_void_p)]
+
+
+class mp_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("op", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class mp_queue_stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in ("submitted", "completed", "failed", "steps", "launches",
+                                               "peak_bytes", "waiting", "active", "bytes_in_use")]
 
 
 class mp_plan(ctypes.Structure):
@@ -81,6 +111,26 @@ _SIGNATURES = {
     "mp_merge_batched": ([_I32, _P, _P, _P, _P, _I64, _I64, _I64, _P, _P, _P, _P,
                           ctypes.POINTER(mp_plan), _P], _I32),
     "mp_check_sorted": ([_I32, _P, _I64, _P], _I32),
+    "mp_merge_grouped": ([ctypes.POINTER(mp_merge_desc), _I64, _I32, _P], _I32),
+    "mp_clock_seconds": ([], ctypes.c_double),
+    "mp_autotune_merge": ([_I32, _P, _P, _I64, _P, _P, _I64, _P, _P, _I32, ctypes.POINTER(mp_plan), _P], _I32),
+    "mp_autotune_batched": ([_I32, _P, _P, _P, _P, _I64, _I64, _I64, _P, _P, _P, _P, _I32,
+                             ctypes.POINTER(mp_plan), _P], _I32),
+    "mp_tune_save": ([ctypes.c_char_p], _I32),
+    "mp_tune_load": ([ctypes.c_char_p], _I32),
+    "mp_tune_clear": ([], None),
+    "mp_graph_merge_create": ([_I32, _P, _P, _I64, _P, _P, _I64, _P, _P, ctypes.POINTER(mp_plan),
+                               ctypes.POINTER(ctypes.c_void_p)], _I32),
+    "mp_graph_batched_create": ([_I32, _P, _P, _P, _P, _I64, _I64, _I64, _P, _P, _P, _P,
+                                 ctypes.POINTER(mp_plan), ctypes.POINTER(ctypes.c_void_p)], _I32),
+    "mp_graph_launch": ([_P, _P], _I32),
+    "mp_graph_destroy": ([_P], _I32),
+    "mp_queue_create": ([_SZ, _I32, ctypes.POINTER(ctypes.c_void_p)], _I32),
+    "mp_queue_submit": ([_P, ctypes.POINTER(mp_request), ctypes.POINTER(ctypes.c_uint64)], _I32),
+    "mp_queue_wait": ([_P, ctypes.c_uint64, _I64, ctypes.POINTER(mp_result)], _I32),
+    "mp_queue_get_stats": ([_P, ctypes.POINTER(mp_queue_stats)], _I32),
+    "mp_queue_destroy": ([_P], _I32),
+    "mp_generate": ([_I32, _P, _P, _I64, ctypes.c_uint64, ctypes.c_uint64, _I32, ctypes.c_uint32, _P], _I32),
 }
 
 
@@ -307,7 +357,263 @@ def mp_merge_batched(a, a_off, b, b_off, out=None, a_vals=None, b_vals=None, out
     return (out, out_vals) if pairs else out
 
 
+def mp_merge_grouped(problems, with_values: bool = False, stream=None):
+    """Merge many independent problems in one launch.  problems: list of
+    (a_keys, b_keys, out_keys) or (a_keys, a_vals, b_keys, b_vals, out_keys,
+    out_vals) tuples of device tensors (one key width for all)."""
+    n = len(problems)
+    arr = (mp_merge_desc * max(n, 1))()
+    for i, pr in enumerate(problems):
+        if with_values:
+            ak, av, bk, bv, ok, ov = pr
+        else:
+            ak, bk, ok = pr
+            av = bv = ov = None
+        d = arr[i]
+        d.dtype = _dtype_code(ak)
+        d.a_keys, d.na = _dev(ak, "a_keys"), ak.numel()
+        d.b_keys, d.nb = _dev(bk, "b_keys"), bk.numel()
+        d.out_keys = _dev(ok, "out_keys")
+        if with_values:
+            d.a_vals, d.b_vals, d.out_vals = _vals(av, "a_vals"), _vals(bv, "b_vals"), _vals(ov, "out_vals")
+    _check(lib().mp_merge_grouped(arr, n, 1 if with_values else 0, _stream(stream)))
+
+
 def mp_check_sorted(keys, stream=None) -> int:
     """Synchronous: MP_OK, MP_ERR_NOT_SORTED or MP_ERR_NAN."""
     return int(lib().mp_check_sorted(_dtype_code(keys), _dev(keys, "keys"), keys.numel(),
                                      _stream(stream)))
+
+
+# --------------------------------------------------------------------- queue
+
+def mp_clock_seconds() -> float:
+    return float(lib().mp_clock_seconds())
+
+
+def mp_queue_create(budget_bytes: int, max_active: int) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().mp_queue_create(int(budget_bytes), int(max_active), ctypes.byref(h)))
+    return h.value
+
+
+def mp_queue_submit(q: int, req: mp_request) -> int:
+    t = ctypes.c_uint64()
+    _check(lib().mp_queue_submit(q, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def mp_queue_wait(q: int, ticket: int, timeout_ns: int = -1) -> mp_result:
+    """Raises MPError (MP_ERR_TIMEOUT / MP_ERR_NOT_READY) if not done in time."""
+    r = mp_result()
+    _check(lib().mp_queue_wait(q, int(ticket), int(timeout_ns), ctypes.byref(r)))
+    return r
+
+
+def mp_queue_get_stats(q: int) -> dict:
+    s = mp_queue_stats()
+    _check(lib().mp_queue_get_stats(q, ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in mp_queue_stats._fields_}
+
+
+def mp_queue_destroy(q: int) -> None:
+    _check(lib().mp_queue_destroy(q))
+
+
+def mp_generate(dtype, keys, n: int, seed: int, stream_id: int, sorted_: bool, vals=None,
+                val_base: int = 0, stream=None):
+    code = dtype if isinstance(dtype, int) else _TORCH_DTYPE[dtype]
+    _check(lib().mp_generate(code, _dev(keys, "keys"), _vals(vals, "vals") if vals is not None else None,
+                             int(n), int(seed), int(stream_id), 1 if sorted_ else 0, int(val_base),
+                             _stream(stream)))
+
+
+def _ptr_any(t):
+    if t is None:
+        return None, None
+    if not t.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return t.data_ptr(), t.is_cuda
+
+
+class Queue:
+    """Convenience wrapper over mp_queue_* (continuous-batching request queue)."""
+
+    def __init__(self, budget_bytes: int, max_active: int = 1024):
+        self.handle = mp_queue_create(budget_bytes, max_active)
+        self._keep = {}
+
+    def _submit(self, req, keep):
+        t = mp_queue_submit(self.handle, req)
+        self._keep[t] = keep
+        return t
+
+    def submit_merge(self, a_keys, b_keys, out_keys, a_vals=None, b_vals=None, out_vals=None):
+        """Inputs and outputs may be host or CUDA tensors (each side's kind
+        is taken from its key tensor)."""
+        r = mp_request()
+        r.op, r.dtype = MP_OP_MERGE, _dtype_code(a_keys)
+        r.with_values = 1 if a_vals is not None else 0
+        r.a_keys, cuda_in = _ptr_any(a_keys)
+        r.b_keys, _ = _ptr_any(b_keys)
+        r.na, r.nb = a_keys.numel(), b_keys.numel()
+        r.source = MP_SRC_DEVICE if cuda_in else MP_SRC_HOST
+        r.out_keys, cuda_out = _ptr_any(out_keys)
+        r.sink = MP_SINK_DEVICE if cuda_out else MP_SINK_HOST
+        if a_vals is not None:
+            r.a_vals, _ = _ptr_any(a_vals)
+            r.b_vals, _ = _ptr_any(b_vals)
+            r.out_vals, _ = _ptr_any(out_vals)
+        return self._submit(r, (a_keys, b_keys, out_keys, a_vals, b_vals, out_vals))
+
+    def submit_sort(self, keys, out_keys, vals=None, out_vals=None):
+        r = mp_request()
+        r.op, r.dtype = MP_OP_SORT, _dtype_code(keys)
+        r.with_values = 1 if vals is not None else 0
+        r.a_keys, cuda_in = _ptr_any(keys)
+        r.na = keys.numel()
+        r.source = MP_SRC_DEVICE if cuda_in else MP_SRC_HOST
+        r.out_keys, cuda_out = _ptr_any(out_keys)
+        r.sink = MP_SINK_DEVICE if cuda_out else MP_SINK_HOST
+        if vals is not None:
+            r.a_vals, _ = _ptr_any(vals)
+            r.out_vals, _ = _ptr_any(out_vals)
+        return self._submit(r, (keys, out_keys, vals, out_vals))
+
+    def submit_generated(self, op: int, dtype: int, na: int, nb: int, seed: int, with_values=True,
+                         out_keys=None, out_vals=None):
+        """Synthetic request generated on the device (mp_generate); result
+        discarded unless output tensors are given."""
+        r = mp_request()
+        r.op, r.dtype, r.with_values = op, dtype, 1 if with_values else 0
+        r.source, r.na, r.nb, r.seed = MP_SRC_GENERATE, int(na), int(nb), int(seed)
+        if out_keys is None:
+            r.sink = MP_SINK_DISCARD
+        else:
+            r.out_keys, cuda_out = _ptr_any(out_keys)
+            r.out_vals, _ = _ptr_any(out_vals)
+            r.sink = MP_SINK_DEVICE if cuda_out else MP_SINK_HOST
+        return self._submit(r, (out_keys, out_vals))
+
+    def wait(self, ticket: int, timeout_s: float | None = None) -> mp_result:
+        ns = -1 if timeout_s is None else int(timeout_s * 1e9)
+        r = mp_queue_wait(self.handle, ticket, ns)
+        self._keep.pop(ticket, None)
+        return r
+
+    def stats(self) -> dict:
+        return mp_queue_get_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            mp_queue_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# --------------------------------------------------------------------- tuning
+
+def mp_autotune_merge(a_keys, b_keys, a_vals=None, b_vals=None, out_keys=None, out_vals=None,
+                      reps: int = 3, stream=None):
+    """Time every compiled tile shape on this problem; returns the best
+    (block_threads, items_per_thread, staging) and records it."""
+    n = a_keys.numel() + b_keys.numel()
+    if out_keys is None:
+        out_keys = torch.empty(n, dtype=a_keys.dtype, device=a_keys.device)
+    pairs = a_vals is not None
+    if pairs and out_vals is None:
+        out_vals = torch.empty(n, dtype=a_vals.dtype, device=a_keys.device)
+    best = mp_plan()
+    _check(lib().mp_autotune_merge(_dtype_code(a_keys), _dev(a_keys, "a_keys"),
+                                   _vals(a_vals, "a_vals") if pairs else None, a_keys.numel(),
+                                   _dev(b_keys, "b_keys"), _vals(b_vals, "b_vals") if pairs else None,
+                                   b_keys.numel(), _dev(out_keys, "out_keys"),
+                                   _vals(out_vals, "out_vals") if pairs else None, int(reps),
+                                   ctypes.byref(best), _stream(stream)))
+    return best.block_threads, best.items_per_thread, best.staging
+
+
+def mp_autotune_batched(a, a_off, b, b_off, out=None, a_vals=None, b_vals=None, out_vals=None,
+                        reps: int = 3, stream=None):
+    nseg = a_off.numel() - 1
+    n = a.numel() + b.numel()
+    if out is None:
+        out = torch.empty(n, dtype=a.dtype, device=a.device)
+    pairs = a_vals is not None
+    if pairs and out_vals is None:
+        out_vals = torch.empty(n, dtype=a_vals.dtype, device=a.device)
+    best = mp_plan()
+    _check(lib().mp_autotune_batched(_dtype_code(a), _dev(a, "a"), _dev(a_off, "a_off"), _dev(b, "b"),
+                                     _dev(b_off, "b_off"), nseg, a.numel(), b.numel(), _dev(out, "out"),
+                                     _vals(a_vals, "a_vals") if pairs else None,
+                                     _vals(b_vals, "b_vals") if pairs else None,
+                                     _vals(out_vals, "out_vals") if pairs else None, int(reps),
+                                     ctypes.byref(best), _stream(stream)))
+    return best.block_threads, best.items_per_thread, best.staging
+
+
+def mp_tune_save(path: str) -> None:
+    _check(lib().mp_tune_save(os.fsencode(path)))
+
+
+def mp_tune_load(path: str) -> None:
+    _check(lib().mp_tune_load(os.fsencode(path)))
+
+
+def mp_tune_clear() -> None:
+    lib().mp_tune_clear()
+
+
+# --------------------------------------------------------------------- graphs
+
+class Graph:
+    """A captured merge (mp_graph_*): replay() enqueues it with one launch."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def replay(self, stream=None):
+        _check(lib().mp_graph_launch(self.handle, _stream(stream)))
+
+    def close(self):
+        if self.handle:
+            _check(lib().mp_graph_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mp_graph_merge_create(a_keys, b_keys, out_keys, a_vals=None, b_vals=None, out_vals=None, plan=None):
+    h = ctypes.c_void_p()
+    pairs = a_vals is not None
+    _check(lib().mp_graph_merge_create(_dtype_code(a_keys), _dev(a_keys, "a_keys"),
+                                       _vals(a_vals, "a_vals") if pairs else None, a_keys.numel(),
+                                       _dev(b_keys, "b_keys"), _vals(b_vals, "b_vals") if pairs else None,
+                                       b_keys.numel(), _dev(out_keys, "out_keys"),
+                                       _vals(out_vals, "out_vals") if pairs else None, _plan(plan),
+                                       ctypes.byref(h)))
+    return Graph(h.value, (a_keys, b_keys, out_keys, a_vals, b_vals, out_vals))
+
+
+def mp_graph_batched_create(a, a_off, b, b_off, out, a_vals=None, b_vals=None, out_vals=None,
+                            plan=None):
+    h = ctypes.c_void_p()
+    pairs = a_vals is not None
+    _check(lib().mp_graph_batched_create(_dtype_code(a), _dev(a, "a"), _dev(a_off, "a_off"), _dev(b, "b"),
+                                         _dev(b_off, "b_off"), a_off.numel() - 1, a.numel(), b.numel(),
+                                         _dev(out, "out"), _vals(a_vals, "a_vals") if pairs else None,
+                                         _vals(b_vals, "b_vals") if pairs else None,
+                                         _vals(out_vals, "out_vals") if pairs else None, _plan(plan),
+                                         ctypes.byref(h)))
+    return Graph(h.value, (a, a_off, b, b_off, out, a_vals, b_vals, out_vals))

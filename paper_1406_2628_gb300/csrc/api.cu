@@ -125,6 +125,13 @@ static mp_status check_merge_args(const KeyKind& k, const void* a, const uint32_
     return MP_OK;
 }
 
+mp_status check_merge_args_ext(const KeyKind& k, const void* a, const uint32_t* av, int64_t na,
+                               const void* b, const uint32_t* bv, int64_t nb, const void* out,
+                               const uint32_t* outv, bool vals, const char* fn)
+{
+    return check_merge_args(k, a, av, na, b, bv, nb, out, outv, vals, fn);
+}
+
 static mp_status resolve_shape(const KeyKind& k, bool vals, int64_t total, const mp_plan* plan, Shape* s)
 {
     *s = default_merge_shape(k.bytes, vals, total);
@@ -139,32 +146,40 @@ static mp_status resolve_shape(const KeyKind& k, bool vals, int64_t total, const
     return MP_OK;
 }
 
-static mp_status merge_impl(mp_dtype dtype, const void* a, const uint32_t* av, int64_t na,
-                            const void* b, const uint32_t* bv, int64_t nb, void* out,
-                            uint32_t* outv, bool vals, const mp_plan* plan, cudaStream_t stream,
-                            const char* fn, const int64_t* given_splits = nullptr)
+mp_status merge_prepare(mp_dtype dtype, const void* a, const uint32_t* av, int64_t na,
+                        const void* b, const uint32_t* bv, int64_t nb, void* out, uint32_t* outv,
+                        bool vals, const mp_plan* plan, const char* fn, MergeProblem* p, Shape* s)
 {
     KeyKind k;
     if (!key_kind(dtype, &k)) return fail(MP_ERR_UNSUPPORTED_DTYPE, std::string(fn) + ": unknown dtype");
     mp_status st = check_merge_args(k, a, av, na, b, bv, nb, out, outv, vals, fn);
     if (st != MP_OK) return st;
-    if (na + nb == 0) return MP_OK;
-    Shape s;
-    st = resolve_shape(k, vals, na + nb, plan, &s);
+    st = resolve_shape(k, vals, na + nb, plan, s);
     if (st != MP_OK) return st;
+    p->kind = k;
+    p->vals = vals;
+    p->a = a;
+    p->b = b;
+    p->av = av;
+    p->bv = bv;
+    p->out = out;
+    p->outv = outv;
+    p->na = na;
+    p->nb = nb;
+    p->run = 0;
+    return MP_OK;
+}
 
+static mp_status merge_impl(mp_dtype dtype, const void* a, const uint32_t* av, int64_t na,
+                            const void* b, const uint32_t* bv, int64_t nb, void* out,
+                            uint32_t* outv, bool vals, const mp_plan* plan, cudaStream_t stream,
+                            const char* fn, const int64_t* given_splits = nullptr)
+{
     MergeProblem p;
-    p.kind = k;
-    p.vals = vals;
-    p.a = a;
-    p.b = b;
-    p.av = av;
-    p.bv = bv;
-    p.out = out;
-    p.outv = outv;
-    p.na = na;
-    p.nb = nb;
-    p.run = 0;
+    Shape s;
+    mp_status st = merge_prepare(dtype, a, av, na, b, bv, nb, out, outv, vals, plan, fn, &p, &s);
+    if (st != MP_OK) return st;
+    if (na + nb == 0) return MP_OK;
     if (given_splits) {
         if (((uintptr_t)given_splits & 7) != 0)
             return fail(MP_ERR_INVALID_ARG, std::string(fn) + ": a_split not 8-byte aligned");

@@ -15,6 +15,7 @@
 //              window, then merges VT outputs, stepping to the next segment
 //              when both sides of the current one are used up.
 #include <algorithm>
+#include <vector>
 
 #include "mp_device.cuh"
 #include "mp_internal.h"
@@ -184,20 +185,6 @@ __global__ void __launch_bounds__(NT) batched_merge_kernel(BatchArgs<K> p)
 // ---------------------------------------------------------------------------
 // Host side.
 // ---------------------------------------------------------------------------
-struct BatchedProblem {
-    KeyKind kind;
-    const void* a;
-    const void* b;
-    const int64_t* a_off;
-    const int64_t* b_off;
-    int64_t nseg, na, nb;
-    void* out;
-    bool vals;
-    const uint32_t* av;
-    const uint32_t* bv;
-    uint32_t* outv;
-};
-
 template <class K>
 static BatchArgs<K> make_batch_args(const BatchedProblem& q, int64_t tile, const int64_t* a_split,
                                     const int64_t* seg_split)
@@ -291,15 +278,10 @@ static cudaError_t launch_batched(const BatchedProblem& q, const Shape& s, int64
     return cudaErrorInvalidValue;
 }
 
-}  // namespace mp
-
-using namespace mp;
-
-extern "C" mp_status mp_merge_batched(mp_dtype dtype, const void* a, const int64_t* a_off,
-                                      const void* b, const int64_t* b_off, int64_t nseg,
-                                      int64_t na_total, int64_t nb_total, void* out,
-                                      const uint32_t* a_vals, const uint32_t* b_vals,
-                                      uint32_t* out_vals, const mp_plan* plan, mp_stream_t stream)
+mp_status batched_prepare(mp_dtype dtype, const void* a, const int64_t* a_off, const void* b,
+                          const int64_t* b_off, int64_t nseg, int64_t na_total, int64_t nb_total,
+                          void* out, const uint32_t* a_vals, const uint32_t* b_vals,
+                          uint32_t* out_vals, const mp_plan* plan, BatchedProblem* q, Shape* s)
 {
     KeyKind k;
     if (!key_kind(dtype, &k)) return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_merge_batched: unknown dtype");
@@ -320,41 +302,126 @@ extern "C" mp_status mp_merge_batched(mp_dtype dtype, const void* a, const int64
         return fail(MP_ERR_INVALID_ARG, "mp_merge_batched: key pointer not aligned to the key size");
     if (vals && (((uintptr_t)a_vals & 3) || ((uintptr_t)b_vals & 3) || ((uintptr_t)out_vals & 3)))
         return fail(MP_ERR_INVALID_ARG, "mp_merge_batched: value pointer not 4-byte aligned");
-    if (na_total + nb_total == 0) return MP_OK;
 
-    Shape s;
-    s.nt = 256;
-    s.vt = k.bytes == 8 ? 8 : 16;
-    s.staging = MP_STAGE_VECTOR;
+    if (!tuned_shape("batched", k.bytes, vals, na_total + nb_total, s)) {
+        s->nt = 256;
+        s->vt = k.bytes == 8 ? 8 : 16;
+        s->staging = MP_STAGE_VECTOR;
+    }
     if (plan) {
         if (plan->reserved) return fail(MP_ERR_INVALID_ARG, "plan.reserved must be 0");
-        if (plan->block_threads) s.nt = plan->block_threads;
-        if (plan->items_per_thread) s.vt = plan->items_per_thread;
-        if (plan->staging) s.staging = plan->staging;
+        if (plan->block_threads) s->nt = plan->block_threads;
+        if (plan->items_per_thread) s->vt = plan->items_per_thread;
+        if (plan->staging) s->staging = plan->staging;
     }
-    if (!batched_shape_supported(s)) return fail(MP_ERR_INVALID_ARG, "mp_merge_batched: unsupported plan");
+    if (!batched_shape_supported(*s)) return fail(MP_ERR_INVALID_ARG, "mp_merge_batched: unsupported plan");
 
+    q->kind = k;
+    q->a = a;
+    q->b = b;
+    q->a_off = a_off;
+    q->b_off = b_off;
+    q->nseg = nseg;
+    q->na = na_total;
+    q->nb = nb_total;
+    q->out = out;
+    q->vals = vals;
+    q->av = a_vals;
+    q->bv = b_vals;
+    q->outv = out_vals;
+    return MP_OK;
+}
+
+size_t batched_scratch_bytes(const BatchedProblem& q, const Shape& s)
+{
+    return (size_t)(ceil_div(q.na + q.nb, s.tile()) + 1) * 16;
+}
+
+cudaError_t batched_launch(const BatchedProblem& q, const Shape& s, void* scratch, cudaStream_t stream)
+{
+    if (q.na + q.nb == 0) return cudaSuccess;
+    const int64_t bounds = ceil_div(q.na + q.nb, s.tile()) + 1;
+    int64_t* sp = static_cast<int64_t*>(scratch);
+    return launch_batched(q, s, sp, sp + bounds, stream);
+}
+
+std::vector<Shape> batched_shapes()
+{
+    std::vector<Shape> v;
+#define X(NT_, VT_) v.push_back(Shape{NT_, VT_, MP_STAGE_VECTOR});
+    MP_BATCHED_SHAPES(X)
+#undef X
+    return v;
+}
+
+}  // namespace mp
+
+using namespace mp;
+
+extern "C" mp_status mp_merge_batched(mp_dtype dtype, const void* a, const int64_t* a_off,
+                                      const void* b, const int64_t* b_off, int64_t nseg,
+                                      int64_t na_total, int64_t nb_total, void* out,
+                                      const uint32_t* a_vals, const uint32_t* b_vals,
+                                      uint32_t* out_vals, const mp_plan* plan, mp_stream_t stream)
+{
     BatchedProblem q;
-    q.kind = k;
-    q.a = a;
-    q.b = b;
-    q.a_off = a_off;
-    q.b_off = b_off;
-    q.nseg = nseg;
-    q.na = na_total;
-    q.nb = nb_total;
-    q.out = out;
-    q.vals = vals;
-    q.av = a_vals;
-    q.bv = b_vals;
-    q.outv = out_vals;
-    const int64_t bounds = ceil_div(na_total + nb_total, s.tile()) + 1;
+    Shape s;
+    mp_status ms = batched_prepare(dtype, a, a_off, b, b_off, nseg, na_total, nb_total, out, a_vals,
+                                   b_vals, out_vals, plan, &q, &s);
+    if (ms != MP_OK || na_total + nb_total == 0) return ms;
     cudaStream_t st = (cudaStream_t)stream;
-    int64_t* scratch = nullptr;
-    mp_status ms = scratch_alloc((void**)&scratch, (size_t)bounds * 16, st);
+    void* scratch = nullptr;
+    ms = scratch_alloc(&scratch, batched_scratch_bytes(q, s), st);
     if (ms != MP_OK) return ms;
-    cudaError_t e = launch_batched(q, s, scratch, scratch + bounds, st);
+    cudaError_t e = batched_launch(q, s, scratch, st);
     scratch_free(scratch, st);
     if (e != cudaSuccess) return cuda_fail(e, "mp_merge_batched");
+    return MP_OK;
+}
+
+extern "C" mp_status mp_autotune_batched(mp_dtype dtype, const void* a, const int64_t* a_off,
+                                         const void* b, const int64_t* b_off, int64_t nseg,
+                                         int64_t na_total, int64_t nb_total, void* out,
+                                         const uint32_t* a_vals, const uint32_t* b_vals,
+                                         uint32_t* out_vals, int reps, mp_plan* best,
+                                         mp_stream_t stream)
+{
+    BatchedProblem q;
+    Shape s;
+    mp_status ms = batched_prepare(dtype, a, a_off, b, b_off, nseg, na_total, nb_total, out, a_vals,
+                                   b_vals, out_vals, nullptr, &q, &s);
+    if (ms != MP_OK) return ms;
+    if (na_total + nb_total == 0) return fail(MP_ERR_INVALID_ARG, "mp_autotune_batched: empty problem");
+    if (reps < 1) reps = 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(MP_ERR_CUDA, "mp_autotune_batched: events");
+    Shape best_s = s;
+    float best_ms = 1e30f;
+    for (const Shape& cand : batched_shapes()) {
+        void* scratch = nullptr;
+        ms = scratch_alloc(&scratch, batched_scratch_bytes(q, cand), st);
+        if (ms != MP_OK) break;
+        cudaError_t e = batched_launch(q, cand, scratch, st);  // warm-up
+        float cand_ms = 1e30f;
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+            cudaEventRecord(e0, st);
+            e = batched_launch(q, cand, scratch, st);
+            cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float t = 0;
+            if (e == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
+            if (e == cudaSuccess && t < cand_ms) cand_ms = t;
+        }
+        scratch_free(scratch, st);
+        if (e != cudaSuccess) { ms = cuda_fail(e, "mp_autotune_batched"); break; }
+        if (cand_ms < best_ms) { best_ms = cand_ms; best_s = cand; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ms != MP_OK) return ms;
+    record_shape("batched", q.kind.bytes, q.vals, na_total + nb_total, best_s);
+    if (best) *best = mp_plan{best_s.nt, best_s.vt, best_s.staging, 0};
     return MP_OK;
 }

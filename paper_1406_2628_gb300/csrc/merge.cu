@@ -9,59 +9,13 @@
 // the window for each thread's VT outputs (Thm 17), merges them serially in
 // registers and writes the tile back with coalesced 128-bit stores.
 #include <algorithm>
+#include <vector>
 
 #include "mp_device.cuh"
 #include "mp_internal.h"
 #include "mp_tile.cuh"
 
 namespace mp {
-
-template <class K>
-struct TileArgs {
-    const K* a;
-    const K* b;
-    const uint32_t* av;
-    const uint32_t* bv;
-    K* out;
-    uint32_t* outv;
-    int64_t na, nb, run;
-    int64_t total;
-    const int64_t* a_split;
-    Codec<K> codec;
-};
-
-// The merge pair that output index d belongs to (run == 0: the only pair).
-template <class K>
-struct Pair {
-    const K* A;
-    const K* B;
-    const uint32_t* AV;
-    const uint32_t* BV;
-    int64_t na, nb, base;
-};
-
-template <class K>
-__device__ __forceinline__ Pair<K> pair_at(const TileArgs<K>& p, int64_t d)
-{
-    Pair<K> q;
-    if (p.run == 0) {
-        q.A = p.a; q.B = p.b; q.AV = p.av; q.BV = p.bv;
-        q.na = p.na; q.nb = p.nb; q.base = 0;
-    } else {
-        const int64_t w2 = 2 * p.run;
-        const int64_t base = (d / w2) * w2;
-        const int64_t rest = p.na - base;
-        q.na = rest < p.run ? rest : p.run;
-        const int64_t rest_b = rest - q.na;
-        q.nb = rest_b < p.run ? rest_b : p.run;
-        q.A = p.a + base;
-        q.B = p.a + base + q.na;
-        q.AV = p.av ? p.av + base : nullptr;
-        q.BV = p.av ? p.av + base + q.na : nullptr;
-        q.base = base;
-    }
-    return q;
-}
 
 // ---------------------------------------------------------------------------
 // Partition: one thread per tile boundary, binary search along the diagonal
@@ -72,15 +26,7 @@ __global__ void __launch_bounds__(256) partition_kernel(TileArgs<K> p, int64_t s
                                                         int64_t n_bounds, int64_t* a_split)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_bounds) return;
-    const int64_t d = t * spacing < p.total ? t * spacing : p.total;
-    const Pair<K> q = pair_at(p, d < p.total ? d : p.total - 1);
-    const K* A = q.A;
-    const K* B = q.B;
-    const Codec<K> c = p.codec;
-    a_split[t] = diagonal_search<K>([&](int64_t i) { return key_enc(__ldg(A + i), c); }, q.na,
-                                    [&](int64_t i) { return key_enc(__ldg(B + i), c); }, q.nb,
-                                    d - q.base);
+    if (t < n_bounds) a_split[t] = partition_point(p, t * spacing);
     // Let a dependent merge launch (programmatic dependent launch) start its
     // prologue; it waits on griddepcontrol.wait before reading a_split.
     asm volatile("griddepcontrol.launch_dependents;");
@@ -92,42 +38,10 @@ __global__ void __launch_bounds__(256) partition_kernel(TileArgs<K> p, int64_t s
 template <class K, bool VALS, int NT, int VT>
 __global__ void __launch_bounds__(NT) merge_tile_kernel(TileArgs<K> p)
 {
-    static_assert(VT % 4 == 0, "VT must be a multiple of 4");
-    constexpr int T = NT * VT;
     extern __shared__ __align__(16) unsigned char smem[];
-
-    const int tid = threadIdx.x;
-    const int64_t tile = blockIdx.x;
-    const int64_t d0 = tile * T;
-    const int64_t d1 = d0 + T < p.total ? d0 + T : p.total;
-    const Pair<K> q = pair_at(p, d0);
-    const int64_t d0l = d0 - q.base, d1l = d1 - q.base;
-
     // Wait for the partition kernel (programmatic dependent launch).
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    // Split points are clamped into the grid and made monotone, so that
-    // unsorted inputs or foreign split arrays give wrong output rather than
-    // out-of-range accesses; for valid inputs the clamps change nothing.
-    const int64_t a0 = clamp_split(p.a_split[tile], d0l, q.na, q.nb);
-    int64_t a1 = (d1l == q.na + q.nb) ? q.na : clamp_split(p.a_split[tile + 1], d1l, q.na, q.nb);
-    a1 = a1 < a0 ? a0 : (a1 > a0 + (d1l - d0l) ? a0 + (d1l - d0l) : a1);
-    const int64_t b0 = d0l - a0, b1 = d1l - a1;
-    const int la = (int)(a1 - a0), lb = (int)(b1 - b0);
-    const int L = la + lb;
-
-    const auto v = stage_tile<K, VALS, NT, VT>(smem, q.A + a0, la, q.B + b0, lb,
-                                               VALS ? q.AV + a0 : nullptr,
-                                               VALS ? q.BV + b0 : nullptr);
-    // Per-thread split inside the window (Thm 17), then VT serial steps.
-    {
-        const int diag = tid * VT < L ? tid * VT : L;
-        const int ai = smem_diagonal_search(v.sA, la, v.sB, lb, diag, p.codec);
-        uint32_t packed[VT / 2];
-        serial_merge_indices<K, VT>(v.sA, la, v.sB, lb, ai, diag - ai, p.codec, packed);
-        put_indices<VT>(v.sidx, packed);
-    }
-    __syncthreads();
-    store_tile<K, VALS, NT, VT>(v, p.out + d0, VALS ? p.outv + d0 : nullptr);
+    merge_tile_body<K, VALS, NT, VT>(p, blockIdx.x, p.a_split, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -208,14 +122,29 @@ bool merge_shape_supported(int key_bytes, bool with_values, const Shape& s)
     return false;
 }
 
+std::vector<Shape> merge_shapes()
+{
+    std::vector<Shape> v;
+#define X(NT_, VT_) v.push_back(Shape{NT_, VT_, MP_STAGE_VECTOR});
+    MP_MERGE_SHAPES(X)
+#undef X
+    return v;
+}
+
 Shape default_merge_shape(int key_bytes, bool with_values, int64_t total)
 {
-    (void)with_values;
-    (void)total;
     Shape s;
-    s.nt = 256;
-    s.vt = key_bytes == 8 ? 8 : 16;
+    if (tuned_shape("merge", key_bytes, with_values, total, &s)) return s;
+    // Shapes with the shortest partition + merge step on GB300 for large
+    // merges (tile-shape sweep); mp_autotune_merge overrides per size class.
     s.staging = MP_STAGE_VECTOR;
+    if (key_bytes == 8) {
+        s.nt = with_values ? 256 : 128;
+        s.vt = 16;
+    } else {
+        s.nt = 256;
+        s.vt = 16;
+    }
     return s;
 }
 

@@ -3,6 +3,7 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -56,11 +57,80 @@ cudaError_t launch_merge_tiles(const MergeProblem& p, const Shape& shape, const 
                                cudaStream_t stream);
 bool merge_shape_supported(int key_bytes, bool with_values, const Shape& shape);
 Shape default_merge_shape(int key_bytes, bool with_values, int64_t total);
+std::vector<Shape> merge_shapes();
+
+// Autotuner cache (tune.cu): op is "merge" or "batched".
+bool tuned_shape(const char* op, int key_bytes, bool vals, int64_t total, Shape* s);
+void record_shape(const char* op, int key_bytes, bool vals, int64_t total, const Shape& s);
+
+// Batched merge (batched.cu): validation, then launch with caller scratch of
+// batched_scratch_bytes() bytes.
+struct BatchedProblem {
+    KeyKind kind;
+    const void* a;
+    const void* b;
+    const int64_t* a_off;
+    const int64_t* b_off;
+    int64_t nseg, na, nb;
+    void* out;
+    bool vals;
+    const uint32_t* av;
+    const uint32_t* bv;
+    uint32_t* outv;
+};
+mp_status batched_prepare(mp_dtype dtype, const void* a, const int64_t* a_off, const void* b,
+                          const int64_t* b_off, int64_t nseg, int64_t na_total, int64_t nb_total,
+                          void* out, const uint32_t* a_vals, const uint32_t* b_vals,
+                          uint32_t* out_vals, const mp_plan* plan, BatchedProblem* q, Shape* s);
+size_t batched_scratch_bytes(const BatchedProblem& q, const Shape& s);
+cudaError_t batched_launch(const BatchedProblem& q, const Shape& s, void* scratch, cudaStream_t stream);
+
+// Plain merge: validation, then launch with caller scratch (split points).
+mp_status merge_prepare(mp_dtype dtype, const void* a, const uint32_t* av, int64_t na,
+                        const void* b, const uint32_t* bv, int64_t nb, void* out, uint32_t* outv,
+                        bool vals, const mp_plan* plan, const char* fn, MergeProblem* p, Shape* s);
 
 // Merge sort.
 size_t sort_workspace_bytes(const KeyKind& kind, int64_t n, bool with_values);
 mp_status sort_run(const KeyKind& kind, void* keys, uint32_t* vals, int64_t n, void* ws,
                    size_t ws_bytes, cudaStream_t stream);
+
+// Grouped launches (grouped.cu): many independent problems, each with its
+// own pointers and codec, one key width per launch.
+struct GroupMergeDesc {
+    const void* a;
+    const void* b;
+    const uint32_t* av;
+    const uint32_t* bv;
+    void* out;
+    uint32_t* outv;
+    int64_t na, nb, run;  // run > 0: sort pass over a[0..na) (see MergeProblem)
+    uint64_t flip, fmask;
+};
+struct GroupSortDesc {
+    const void* in;
+    const uint32_t* vin;
+    void* out;
+    uint32_t* vout;
+    int64_t n;
+    uint64_t flip, fmask;
+};
+// tile_first[p]: first tile of problem p (prefix of ceil(total/T));
+// bound_first[p] = tile_first[p] + p; d_splits: total_tiles + nprob int64.
+cudaError_t launch_grouped_merge(int key_bytes, bool vals, const GroupMergeDesc* d_descs,
+                                 const int64_t* d_tile_first, const int64_t* d_bound_first,
+                                 int nprob, int64_t total_tiles, int64_t* d_splits,
+                                 cudaStream_t stream);
+cudaError_t launch_grouped_block_sort(int key_bytes, bool vals, const GroupSortDesc* d_descs,
+                                      const int64_t* d_tile_first, int nprob, int64_t total_tiles,
+                                      cudaStream_t stream);
+int64_t grouped_merge_tile(int key_bytes);
+int64_t grouped_sort_tile(int key_bytes);
+
+// Merge argument checks (api.cu).
+mp_status check_merge_args_ext(const KeyKind& k, const void* a, const uint32_t* av, int64_t na,
+                               const void* b, const uint32_t* bv, int64_t nb, const void* out,
+                               const uint32_t* outv, bool vals, const char* fn);
 
 // Errors: record a detail for mp_last_error() and return the status.
 mp_status fail(mp_status st, const std::string& detail);

@@ -13,6 +13,68 @@
 
 namespace mp {
 
+template <class K>
+struct TileArgs {
+    const K* a;
+    const K* b;
+    const uint32_t* av;
+    const uint32_t* bv;
+    K* out;
+    uint32_t* outv;
+    int64_t na, nb, run;
+    int64_t total;
+    const int64_t* a_split;
+    Codec<K> codec;
+};
+
+// The merge pair that output index d belongs to (run == 0: the only pair).
+template <class K>
+struct Pair {
+    const K* A;
+    const K* B;
+    const uint32_t* AV;
+    const uint32_t* BV;
+    int64_t na, nb, base;
+};
+
+template <class K>
+__device__ __forceinline__ Pair<K> pair_at(const TileArgs<K>& p, int64_t d)
+{
+    Pair<K> q;
+    if (p.run == 0) {
+        q.A = p.a; q.B = p.b; q.AV = p.av; q.BV = p.bv;
+        q.na = p.na; q.nb = p.nb; q.base = 0;
+    } else {
+        const int64_t w2 = 2 * p.run;
+        const int64_t base = (d / w2) * w2;
+        const int64_t rest = p.na - base;
+        q.na = rest < p.run ? rest : p.run;
+        const int64_t rest_b = rest - q.na;
+        q.nb = rest_b < p.run ? rest_b : p.run;
+        q.A = p.a + base;
+        q.B = p.a + base + q.na;
+        q.AV = p.av ? p.av + base : nullptr;
+        q.BV = p.av ? p.av + base + q.na : nullptr;
+        q.base = base;
+    }
+    return q;
+}
+
+// Split point (Alg. 2) of output index d, clamped to [0, total], relative to
+// the merge pair holding d.
+template <class K>
+__device__ __forceinline__ int64_t partition_point(const TileArgs<K>& p, int64_t d)
+{
+    d = d < p.total ? d : p.total;
+    const Pair<K> q = pair_at(p, d < p.total ? d : p.total - 1);
+    const K* A = q.A;
+    const K* B = q.B;
+    const Codec<K> c = p.codec;
+    return diagonal_search<K>([&](int64_t i) { return key_enc(__ldg(A + i), c); }, q.na,
+                              [&](int64_t i) { return key_enc(__ldg(B + i), c); }, q.nb,
+                              d - q.base);
+}
+
 // Shared memory of a tile: keys [T + 3*EK] (room for the two windows at
 // their 16-byte phases), values [T + 12] (if VALS), source indices [T] u16.
 template <class K, bool VALS, int NT, int VT>
@@ -161,6 +223,45 @@ __device__ __forceinline__ void store_tile(const TileView<K, VALS, NT, VT>& v, K
             }
         }
     }
+}
+
+// One tile of a merge problem (plain merge or sort pass): stage, split,
+// merge, store.  a_split holds the problem's split points at multiples of T.
+template <class K, bool VALS, int NT, int VT>
+__device__ __forceinline__ void merge_tile_body(const TileArgs<K>& p, int64_t tile,
+                                                const int64_t* a_split, unsigned char* smem)
+{
+    static_assert(VT % 4 == 0, "VT must be a multiple of 4");
+    constexpr int T = NT * VT;
+    const int tid = threadIdx.x;
+    const int64_t d0 = tile * T;
+    const int64_t d1 = d0 + T < p.total ? d0 + T : p.total;
+    const Pair<K> q = pair_at(p, d0);
+    const int64_t d0l = d0 - q.base, d1l = d1 - q.base;
+
+    // Split points are clamped into the grid and made monotone, so that
+    // unsorted inputs or foreign split arrays give wrong output rather than
+    // out-of-range accesses; for valid inputs the clamps change nothing.
+    const int64_t a0 = clamp_split(a_split[tile], d0l, q.na, q.nb);
+    int64_t a1 = (d1l == q.na + q.nb) ? q.na : clamp_split(a_split[tile + 1], d1l, q.na, q.nb);
+    a1 = a1 < a0 ? a0 : (a1 > a0 + (d1l - d0l) ? a0 + (d1l - d0l) : a1);
+    const int64_t b0 = d0l - a0, b1 = d1l - a1;
+    const int la = (int)(a1 - a0), lb = (int)(b1 - b0);
+    const int L = la + lb;
+
+    const auto v = stage_tile<K, VALS, NT, VT>(smem, q.A + a0, la, q.B + b0, lb,
+                                               VALS ? q.AV + a0 : nullptr,
+                                               VALS ? q.BV + b0 : nullptr);
+    // Per-thread split inside the window (Thm 17), then VT serial steps.
+    {
+        const int diag = tid * VT < L ? tid * VT : L;
+        const int ai = smem_diagonal_search(v.sA, la, v.sB, lb, diag, p.codec);
+        uint32_t packed[VT / 2];
+        serial_merge_indices<K, VT>(v.sA, la, v.sB, lb, ai, diag - ai, p.codec, packed);
+        put_indices<VT>(v.sidx, packed);
+    }
+    __syncthreads();
+    store_tile<K, VALS, NT, VT>(v, p.out + d0, VALS ? p.outv + d0 : nullptr);
 }
 
 }  // namespace mp

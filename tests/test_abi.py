@@ -4,6 +4,7 @@ queries behave as documented (these return before any CUDA call)."""
 import ctypes
 import os
 import re
+from ctypes import byref as C_byref, c_void_p as C_void_p
 
 import pytest
 
@@ -117,3 +118,35 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(mp, "LIB_PATH", str(tmp_path / "libmp.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         mp.lib()
+
+
+def test_tune_table_round_trip_on_host(lib, tmp_path):
+    """The tuned-shape table is host state: an entry loaded from a file is
+    what automatic plans use (no GPU needed to resolve a plan)."""
+    mp.mp_tune_clear()
+    default = lib.mp_merge_tile_items(mp.MP_I32, 0, 1 << 20, None)
+    assert default > 0
+    # The device name is "unknown" when no GPU is visible.
+    path = tmp_path / "tune.txt"
+    path.write_text("unknown|merge|4|0|20 128 8 1\n")
+    mp.mp_tune_load(str(path))
+    try:
+        assert lib.mp_merge_tile_items(mp.MP_I32, 0, 1 << 20, None) == 1024
+        assert lib.mp_merge_tile_items(mp.MP_I32, 0, 1 << 21, None) == default
+        mp.mp_tune_save(str(tmp_path / "out.txt"))
+        assert "unknown|merge|4|0|20 128 8 1" in (tmp_path / "out.txt").read_text()
+    finally:
+        mp.mp_tune_clear()
+    with pytest.raises(mp.MPError):
+        mp.mp_tune_load(str(tmp_path / "missing.txt"))
+
+
+def test_queue_argument_errors(lib):
+    h = C_void_p()
+    assert lib.mp_queue_create(0, 4, C_byref(h)) == mp.MP_ERR_INVALID_ARG
+    assert lib.mp_queue_create(1 << 20, 0, C_byref(h)) == mp.MP_ERR_INVALID_ARG
+    assert lib.mp_queue_submit(None, None, None) == mp.MP_ERR_INVALID_ARG
+    assert lib.mp_queue_wait(None, 1, 0, None) == mp.MP_ERR_INVALID_ARG
+    assert lib.mp_queue_destroy(None) == mp.MP_OK
+    assert lib.mp_graph_launch(None, None) == mp.MP_ERR_INVALID_ARG
+    assert lib.mp_graph_destroy(None) == mp.MP_OK
