@@ -64,6 +64,11 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--plan", default=None, help="NT,VT tile plan (default: automatic)")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the other workloads (plain keys, sort, batched, serving)")
+    p.add_argument("--extras", default="plain,sort,batched,serving",
+                   help="comma list of extra workloads to run after the headline")
+    p.add_argument("--serving-requests", type=int, default=50000)
     return p.parse_args()
 
 
@@ -100,7 +105,9 @@ def recorded_traffic(workload_key):
 
 
 class ClockSampler:
-    """nvidia-smi SM clock / throttle samples every 100 ms in the background."""
+    """nvidia-smi SM clock / throttle samples every 100 ms in the background,
+    kept for the span from the first warm-up step to the end of a ~1 s soak
+    of the same step after the timed region and the per-kernel timing."""
 
     FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -240,6 +247,282 @@ def run_reference(args):
     return 0
 
 
+# --------------------------------------------------------------------- extras
+#
+# The other workloads, reported under "extras" in the same JSON line.  Inputs
+# for these are generated on the device (torch / mp_generate): they measure
+# speed; their exactness is covered by the parity tests.
+
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def extra_plain(mp, torch, dev, reps=50):
+    """2 x 2^20 int32 keys, uniform in [0, 2^24), sorted; warm (L2-resident)
+    and cold (L2 flushed by a 512 MB write before each call)."""
+    import gen
+    a, b = gen.plain_keys()
+    A, B = torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)
+    out = torch.empty(a.size + b.size, dtype=torch.int32, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(5):
+        mp.mp_merge_keys(A, B, out)
+    e0, e1 = _events(torch)
+    e0.record()
+    for _ in range(reps):
+        mp.mp_merge_keys(A, B, out)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    warm_us = e0.elapsed_time(e1) / reps * 1e3
+    cold = []
+    for _ in range(reps // 2):
+        flush.fill_(1)
+        e0.record()
+        mp.mp_merge_keys(A, B, out)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        cold.append(e0.elapsed_time(e1) * 1e3)
+    n = a.size + b.size
+    cold_us = statistics.median(cold)
+    return {"n": n, "warm_us": warm_us, "cold_us": cold_us, "gkeys_s_warm": n / warm_us / 1e3,
+            "gkeys_s_cold": n / cold_us / 1e3, "gbs_cold": 2 * n * 4 / cold_us / 1e3}
+
+
+def _device_sort_input(torch, dev, dtype, order, n, seed):
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    if dtype == "i32":
+        x = torch.randint(-(1 << 31), 1 << 31, (n,), dtype=torch.int64, device=dev, generator=g).to(torch.int32)
+    else:
+        bits = torch.randint(-(1 << 31), 1 << 31, (n,), dtype=torch.int64, device=dev, generator=g).to(torch.int32)
+        x = bits.view(torch.float32)
+        nan = torch.isnan(x)
+        x[nan] = 1.0  # NaN excluded from the key order
+    if order == "sorted":
+        x = torch.sort(x).values
+    elif order == "reverse":
+        x = torch.sort(x, descending=True).values
+    elif order == "distinct256":
+        vals = x[:256].clone()
+        idx = torch.randint(0, 256, (n,), device=dev, generator=g)
+        x = vals[idx]
+    return x.contiguous()
+
+
+def extra_sort(mp, torch, dev, n=1 << 28, reps=3):
+    res = {}
+    work = None
+    ws = None
+    for dtype in ("i32", "f32"):
+        for order in ("random", "sorted", "reverse", "distinct256"):
+            x = _device_sort_input(torch, dev, dtype, order, n, 1234)
+            if work is None:
+                work = torch.empty_like(x)
+                ws = torch.empty(mp.mp_sort_workspace_bytes(torch.int32, n, False), dtype=torch.uint8, device=dev)
+            w = work.view(x.dtype)
+            times = []
+            for r in range(reps + 1):
+                w.copy_(x)
+                e0, e1 = _events(torch)
+                e0.record()
+                mp.mp_sort(w, workspace=ws)
+                e1.record()
+                torch.cuda.synchronize(dev)
+                if r:
+                    times.append(e0.elapsed_time(e1))
+            ms = min(times)
+            blocks = (n + 4095) // 4096
+            passes = 1 + max(0, math.ceil(math.log2(blocks)))
+            res[f"{dtype}_{order}"] = {"ms": ms, "gkeys_s": n / ms / 1e6,
+                                       "eff_gbs": passes * 2 * n * 4 / ms / 1e6, "hbm_passes": passes}
+            del x
+    res["n"] = n
+    return res
+
+
+def extra_batched(mp, torch, dev, n_seg=16384, log2_max=18.0, reps=5):
+    """16,384 int32 merge pairs, per-side length floor(2^U), U ~ U[0, 18];
+    one batched call, its CUDA-graph replay, a grouped launch, and 16,384
+    per-call mp_merge_keys launches."""
+    import gen
+    la, lb = gen.batched_lengths(n_seg, log2_max)
+    a_off = np.concatenate([[0], np.cumsum(la)]).astype(np.int64)
+    b_off = np.concatenate([[0], np.cumsum(lb)]).astype(np.int64)
+
+    def side(lens, seed):
+        g = torch.Generator(device=dev)
+        g.manual_seed(seed)
+        total = int(lens.sum())
+        keys = torch.randint(0, 1 << 31, (total,), dtype=torch.int64, device=dev, generator=g)
+        seg = torch.repeat_interleave(torch.arange(lens.size, device=dev), torch.from_numpy(lens).to(dev))
+        return (torch.sort((seg << 32) | keys).values & 0xFFFFFFFF).to(torch.int32)
+
+    A, B = side(la, 41), side(lb, 42)
+    AO, BO = torch.from_numpy(a_off).to(dev), torch.from_numpy(b_off).to(dev)
+    n = A.numel() + B.numel()
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    for _ in range(2):
+        mp.mp_merge_batched(A, AO, B, BO, out=out)
+    e0, e1 = _events(torch)
+    e0.record()
+    for _ in range(reps):
+        mp.mp_merge_batched(A, AO, B, BO, out=out)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    batched_ms = e0.elapsed_time(e1) / reps
+    g = mp.mp_graph_batched_create(A, AO, B, BO, out)
+    g.replay()
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    graph_ms = e0.elapsed_time(e1) / reps
+    g.close()
+    # Per-call baseline and grouped launch over the same segments.
+    ao, bo = a_off.tolist(), b_off.tolist()
+    views = [(A[ao[s]:ao[s + 1]], B[bo[s]:bo[s + 1]], out[ao[s] + bo[s]:ao[s + 1] + bo[s + 1]])
+             for s in range(n_seg)]
+    mp.mp_merge_grouped(views)
+    e0.record()
+    mp.mp_merge_grouped(views)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    grouped_ms = e0.elapsed_time(e1)
+    for v in views[:64]:
+        mp.mp_merge_keys(*v)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e0.record()
+    for v in views:
+        mp.mp_merge_keys(v[0], v[1], v[2])
+    e1.record()
+    torch.cuda.synchronize(dev)
+    per_call_ms = e0.elapsed_time(e1)
+    per_call_wall_ms = (time.perf_counter() - t0) * 1e3
+    byt = 2 * n * 4
+    return {"segments": n_seg, "keys": n, "batched_ms": batched_ms, "graph_ms": graph_ms,
+            "grouped_ms": grouped_ms, "per_call_ms": per_call_ms, "per_call_wall_ms": per_call_wall_ms,
+            "batched_gkeys_s": n / batched_ms / 1e6, "batched_gbs": byt / batched_ms / 1e6,
+            "graph_gbs": byt / graph_ms / 1e6, "per_call_gbs": byt / per_call_ms / 1e6,
+            "speedup_batched_vs_per_call": per_call_ms / batched_ms,
+            "speedup_graph_vs_per_call": per_call_ms / graph_ms}
+
+
+def _serving_trace(n_req, seed=0x5E7):
+    import gen
+    u = (gen.splitmix64(seed, 1, n_req) >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+    is_sort = u < 0.3
+    def logu(stream):
+        v = (gen.splitmix64(seed, stream, n_req) >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+        return np.floor(np.exp2(10 + 14 * v)).astype(np.int64)
+    na, nb = logu(2), logu(3)
+    nb[is_sort] = 0
+    return is_sort, na, nb
+
+
+def _run_queue_trace(mp, is_sort, na, nb, arrivals, budget, max_active=4096):
+    """Submit each request at its arrival time (seconds from t0); returns
+    per-request latencies (done - arrival) and the makespan."""
+    q = mp.Queue(budget_bytes=budget, max_active=max_active)
+    n_req = len(na)
+    tickets = [None] * n_req
+    results = [None] * n_req
+    t0 = mp.mp_clock_seconds() + 0.05
+
+    def waiter():
+        for i in range(n_req):
+            while tickets[i] is None:
+                time.sleep(0.0002)
+            results[i] = q.wait(tickets[i])
+
+    th = threading.Thread(target=waiter, daemon=True)
+    th.start()
+    i = 0
+    while i < n_req:
+        now = mp.mp_clock_seconds() - t0
+        while i < n_req and arrivals[i] <= now:
+            op = mp.MP_OP_SORT if is_sort[i] else mp.MP_OP_MERGE
+            tickets[i] = q.submit_generated(op, mp.MP_U32, int(na[i]), int(nb[i]), seed=i, with_values=True)
+            i += 1
+        if i < n_req:
+            wait = arrivals[i] - (mp.mp_clock_seconds() - t0)
+            if wait > 0.0005:
+                time.sleep(wait - 0.0003)
+    th.join()
+    stats = q.stats()
+    q.close()
+    lat = np.array([results[j].t_done - (t0 + arrivals[j]) for j in range(n_req)])
+    bad = sum(1 for r in results if r.status != 0)
+    makespan = max(r.t_done for r in results) - t0
+    return lat, makespan, stats, bad
+
+
+def _run_serial_trace(mp, torch, dev, is_sort, na, nb, arrivals):
+    """The same trace served one request at a time with plain calls (inputs
+    generated on the device by the same generator, then mp_merge_pairs or
+    mp_sort), each finished before the next starts."""
+    maxn = int(max((na + nb).max(), 2))
+    ka = torch.empty(maxn, dtype=torch.int32, device=dev)
+    kb = torch.empty(maxn, dtype=torch.int32, device=dev)
+    va = torch.empty(maxn, dtype=torch.int32, device=dev)
+    vb = torch.empty(maxn, dtype=torch.int32, device=dev)
+    ko = torch.empty(maxn, dtype=torch.int32, device=dev)
+    vo = torch.empty(maxn, dtype=torch.int32, device=dev)
+    ws = torch.empty(mp.mp_sort_workspace_bytes(mp.MP_U32, maxn, True), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    n_req = len(na)
+    lat = np.zeros(n_req)
+    t0 = mp.mp_clock_seconds() + 0.05
+    for i in range(n_req):
+        while mp.mp_clock_seconds() - t0 < arrivals[i]:
+            pass
+        a, b = int(na[i]), int(nb[i])
+        if is_sort[i]:
+            mp.mp_generate(mp.MP_U32, ka, a, i, 3, False, vals=va, val_base=0)
+            k = ka[:a].view(torch.uint32)
+            mp.mp_sort(k, va[:a], workspace=ws)
+        else:
+            mp.mp_generate(mp.MP_U32, ka, a, i, 1, True, vals=va, val_base=0)
+            mp.mp_generate(mp.MP_U32, kb, b, i, 2, True, vals=vb, val_base=a)
+            mp.mp_merge_pairs(ka[:a].view(torch.uint32), va[:a], kb[:b].view(torch.uint32), vb[:b],
+                              ko[:a + b].view(torch.uint32), vo[:a + b])
+        stream.synchronize()
+        lat[i] = mp.mp_clock_seconds() - (t0 + arrivals[i])
+    makespan = mp.mp_clock_seconds() - t0
+    return lat, makespan
+
+
+def extra_serving(mp, torch, dev, n_req=50000, budget=8 << 30, rhos=(0.5, 0.9)):
+    """Poisson arrivals of merge (70 %) and sort (30 %) requests, uint32 keys
+    + uint32 values, sizes log-uniform in [2^10, 2^24], generated on the
+    device at admission; the queue (continuous batching under an 8 GB
+    budget) against serial per-request plain calls on the same trace."""
+    is_sort, na, nb = _serving_trace(n_req)
+    items = int((na + nb).sum())
+    # Capacity: the whole trace submitted at once (closed loop).
+    lat, makespan, st, bad = _run_queue_trace(mp, is_sort, na, nb, np.zeros(n_req), budget)
+    cap_req_s = n_req / makespan
+    out = {"requests": n_req, "items": items, "budget_bytes": budget,
+           "capacity": {"req_s": cap_req_s, "gitems_s": items / makespan / 1e9, "makespan_s": makespan,
+                        "steps": st["steps"], "launches": st["launches"], "failed": bad}}
+    rng = np.random.default_rng(7)
+    for rho in rhos:
+        lam = rho * cap_req_s
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, n_req))
+        arrivals -= arrivals[0]
+        lat, makespan, st, bad = _run_queue_trace(mp, is_sort, na, nb, arrivals, budget)
+        slat, smake = _run_serial_trace(mp, torch, dev, is_sort, na, nb, arrivals)
+        out[f"rho_{rho}"] = {
+            "rate_req_s": lam,
+            "queue": {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                      "throughput_gitems_s": items / makespan / 1e9, "makespan_s": makespan,
+                      "steps": st["steps"], "failed": bad},
+            "serial": {"p50_ms": float(np.percentile(slat, 50) * 1e3), "p99_ms": float(np.percentile(slat, 99) * 1e3),
+                       "throughput_gitems_s": items / smake / 1e9, "makespan_s": smake}}
+    return out
+
+
 # --------------------------------------------------------------------- ours
 
 def run_ours(args):
@@ -321,9 +604,17 @@ def run_ours(args):
         mp.mp_merge_partitioned(A, B, splits, AV, BV, OK, OV, plan=plan)
     e2.record(stream)
     torch.cuda.synchronize(dev)
-    t_load1 = time.time()
     part_ms = e0.elapsed_time(e1) / reps
     merge_ms = e1.elapsed_time(e2) / reps
+    # The timed region is short next to the sampler's 100 ms period: keep the
+    # same step running for about a second more so the clock record covers
+    # this kernel under load.
+    soak_end = time.time() + 1.2
+    while time.time() < soak_end:
+        for _ in range(20):
+            step()
+        torch.cuda.synchronize(dev)
+    t_load1 = time.time()
     sampler.stop()
     clocks = sampler.summary(t_load0, t_load1)
 
@@ -378,6 +669,23 @@ def run_ours(args):
     }
     if e2e is not None:
         line["e2e"] = e2e
+    if not args.no_extras:
+        extras = {}
+        wanted = [x for x in args.extras.split(",") if x]
+        runners = {"plain": lambda: extra_plain(mp, torch, dev),
+                   "sort": lambda: extra_sort(mp, torch, dev),
+                   "batched": lambda: extra_batched(mp, torch, dev),
+                   "serving": lambda: extra_serving(mp, torch, dev, n_req=args.serving_requests)}
+        del OK, OV
+        for name in wanted:
+            t0 = time.perf_counter()
+            try:
+                extras[name] = runners[name]()
+            except Exception as exc:  # an extra never breaks the headline line
+                extras[name] = {"error": f"{type(exc).__name__}: {exc}"}
+            extras[name]["wall_s"] = time.perf_counter() - t0
+            torch.cuda.empty_cache()
+        line["extras"] = extras
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, reps_o, secs = oracle_rate(a, av, b, bv)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
