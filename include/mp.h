@@ -294,6 +294,15 @@ MP_API mp_status mp_graph_launch(mp_graph* graph, mp_stream_t stream);
 /* Waits for the device, then frees the graph and its scratch. */
 MP_API mp_status mp_graph_destroy(mp_graph* graph);
 
+/*
+ * mp_kernel_error -- SYNCHRONOUS (waits for the device).  Bit flags set by
+ * kernels whose bounded waits ran out (1: an mbarrier wait of the TMA-staged
+ * merge timed out; the CTA stopped early and its tiles are incomplete).
+ * 0 means no kernel reported a problem since the last reset.  reset != 0
+ * clears the flags after reading them.
+ */
+MP_API mp_status mp_kernel_error(unsigned int* code, int reset);
+
 /* One problem of mp_merge_grouped. */
 typedef struct mp_merge_desc {
     int32_t dtype;    /* mp_dtype of this problem's keys */

@@ -113,6 +113,7 @@ _SIGNATURES = {
     "mp_check_sorted": ([_I32, _P, _I64, _P], _I32),
     "mp_merge_grouped": ([ctypes.POINTER(mp_merge_desc), _I64, _I32, _P], _I32),
     "mp_clock_seconds": ([], ctypes.c_double),
+    "mp_kernel_error": ([ctypes.POINTER(ctypes.c_uint), _I32], _I32),
     "mp_autotune_merge": ([_I32, _P, _P, _I64, _P, _P, _I64, _P, _P, _I32, ctypes.POINTER(mp_plan), _P], _I32),
     "mp_autotune_batched": ([_I32, _P, _P, _P, _P, _I64, _I64, _I64, _P, _P, _P, _P, _I32,
                              ctypes.POINTER(mp_plan), _P], _I32),
@@ -386,6 +387,13 @@ def mp_check_sorted(keys, stream=None) -> int:
 
 
 # --------------------------------------------------------------------- queue
+
+def mp_kernel_error(reset: bool = False) -> int:
+    """Synchronous: flags set by kernels whose bounded waits ran out (0 = none)."""
+    v = ctypes.c_uint()
+    _check(lib().mp_kernel_error(ctypes.byref(v), 1 if reset else 0))
+    return v.value
+
 
 def mp_clock_seconds() -> float:
     return float(lib().mp_clock_seconds())

@@ -14,8 +14,11 @@
 #include "mp_device.cuh"
 #include "mp_internal.h"
 #include "mp_tile.cuh"
+#include "mp_bulk.cuh"
 
 namespace mp {
+
+__device__ unsigned int g_mp_kernel_error = 0;
 
 // ---------------------------------------------------------------------------
 // Partition: one thread per tile boundary, binary search along the diagonal
@@ -42,6 +45,30 @@ __global__ void __launch_bounds__(NT) merge_tile_kernel(TileArgs<K> p)
     // Wait for the partition kernel (programmatic dependent launch).
     asm volatile("griddepcontrol.wait;" ::: "memory");
     merge_tile_body<K, VALS, NT, VT>(p, blockIdx.x, p.a_split, smem);
+}
+
+// Persistent variant: windows staged by TMA bulk copies, double-buffered.
+template <class K, bool VALS, int NT, int VT>
+__global__ void __launch_bounds__(NT) merge_tile_bulk_kernel(TileArgs<K> p, int64_t ntiles,
+                                                              unsigned int* err)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    merge_tiles_bulk<K, VALS, NT, VT>(p, ntiles, p.a_split, smem, err);
+}
+
+// Device address of the kernel error word on the current device.
+static unsigned int* kernel_error_word()
+{
+    static unsigned int* addr[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_mp_kernel_error) != cudaSuccess) return nullptr;
+        addr[dev] = static_cast<unsigned int*>(p);
+    }
+    return addr[dev];
 }
 
 // ---------------------------------------------------------------------------
@@ -108,16 +135,55 @@ static cudaError_t launch_tiles_t(const MergeProblem& p, const int64_t* a_split,
     return cudaLaunchKernelEx(&cfg, kern, make_args<K>(p, a_split));
 }
 
-// Compiled tile shapes (NT, VT).
+template <class K, bool VALS, int NT, int VT>
+static cudaError_t launch_bulk_t(const MergeProblem& p, const int64_t* a_split, cudaStream_t stream)
+{
+    using SM = BulkSmem<K, VALS, NT, VT>;
+    auto kern = merge_tile_bulk_kernel<K, VALS, NT, VT>;
+    static int blocks_per_sm = 0;
+    static int num_sms = 0;
+    if (blocks_per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, NT, SM::bytes);
+        if (e != cudaSuccess) return e;
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    const int64_t tiles = ceil_div(p.total(), (int64_t)NT * VT);
+    const int64_t grid = std::min<int64_t>(tiles, (int64_t)num_sms * blocks_per_sm);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = SM::bytes;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    unsigned int* err = kernel_error_word();
+    if (!err) return cudaErrorInvalidSymbol;
+    return cudaLaunchKernelEx(&cfg, kern, make_args<K>(p, a_split), tiles, err);
+}
+
+// Compiled tile shapes (NT, VT): vector staging and TMA bulk staging.
 #define MP_MERGE_SHAPES(X) X(128, 8) X(256, 8) X(128, 16) X(256, 16) X(512, 8)
+#define MP_BULK_SHAPES(X) X(128, 8) X(256, 8) X(128, 16) X(256, 16)
 
 bool merge_shape_supported(int key_bytes, bool with_values, const Shape& s)
 {
     (void)with_values;
     if (key_bytes != 4 && key_bytes != 8) return false;
-    if (s.staging != MP_STAGE_VECTOR) return false;
 #define X(NT_, VT_) if (s.nt == NT_ && s.vt == VT_) return true;
-    MP_MERGE_SHAPES(X)
+    if (s.staging == MP_STAGE_VECTOR) {
+        MP_MERGE_SHAPES(X)
+    } else if (s.staging == MP_STAGE_BULK) {
+        MP_BULK_SHAPES(X)
+    }
 #undef X
     return false;
 }
@@ -127,6 +193,9 @@ std::vector<Shape> merge_shapes()
     std::vector<Shape> v;
 #define X(NT_, VT_) v.push_back(Shape{NT_, VT_, MP_STAGE_VECTOR});
     MP_MERGE_SHAPES(X)
+#undef X
+#define X(NT_, VT_) v.push_back(Shape{NT_, VT_, MP_STAGE_BULK});
+    MP_BULK_SHAPES(X)
 #undef X
     return v;
 }
@@ -152,6 +221,19 @@ cudaError_t launch_merge_tiles(const MergeProblem& p, const Shape& s, const int6
                                cudaStream_t stream)
 {
     const bool vals = p.vals;
+    if (s.staging == MP_STAGE_BULK) {
+#define X(NT_, VT_)                                                                            \
+        if (s.nt == NT_ && s.vt == VT_) {                                                      \
+            if (p.kind.bytes == 4)                                                             \
+                return vals ? launch_bulk_t<uint32_t, true, NT_, VT_>(p, a_split, stream)      \
+                            : launch_bulk_t<uint32_t, false, NT_, VT_>(p, a_split, stream);    \
+            return vals ? launch_bulk_t<uint64_t, true, NT_, VT_>(p, a_split, stream)          \
+                        : launch_bulk_t<uint64_t, false, NT_, VT_>(p, a_split, stream);        \
+        }
+        MP_BULK_SHAPES(X)
+#undef X
+        return cudaErrorInvalidValue;
+    }
 #define X(NT_, VT_)                                                                            \
     if (s.nt == NT_ && s.vt == VT_) {                                                          \
         if (p.kind.bytes == 4)                                                                 \
@@ -166,3 +248,17 @@ cudaError_t launch_merge_tiles(const MergeProblem& p, const Shape& s, const int6
 }
 
 }  // namespace mp
+
+extern "C" mp_status mp_kernel_error(unsigned int* code, int reset)
+{
+    unsigned int v = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&v, mp::g_mp_kernel_error, sizeof v);
+    if (e == cudaSuccess && reset) {
+        unsigned int z = 0;
+        e = cudaMemcpyToSymbol(mp::g_mp_kernel_error, &z, sizeof z);
+    }
+    if (e != cudaSuccess) return mp::cuda_fail(e, "mp_kernel_error");
+    if (code) *code = v;
+    return MP_OK;
+}

@@ -1,0 +1,293 @@
+// mp_bulk.cuh -- persistent merge tiles staged by TMA bulk copies.
+//
+// Same Merge Path tile as mp_tile.cuh (one CTA-tile = one path segment,
+// Cor. 6; windows bounded by Lemma 16; per-thread splits by Thm 17), but the
+// windows are moved by the Tensor Memory Accelerator: one thread issues a
+// 1D bulk copy (cp.async.bulk) of each window's 16-byte-aligned interior,
+// completion is tracked by an mbarrier, and the ragged edges (< 16 bytes per
+// side) are loaded by a few threads.  Each CTA walks tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ... with two shared-memory stages, so the bulk
+// copies of tile i+1 run while tile i is merged and stored.
+#pragma once
+
+#include "mp_tile.cuh"
+
+namespace mp {
+
+// Bit set in the kernel error word when a bounded wait runs out.
+#define MP_KERR_MBAR_TIMEOUT 1u
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t tx)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(tx)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Waits for the phase with the given parity, at most `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit)
+{
+    for (uint32_t i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Where one tile's windows live in global and in shared memory.
+template <class K>
+struct TilePlace {
+    const K* gA;
+    const K* gB;
+    const uint32_t* gvA;
+    const uint32_t* gvB;
+    int la, lb;
+    int64_t d0;  // first output of the tile
+};
+
+template <class K>
+__device__ __forceinline__ TilePlace<K> tile_place(const TileArgs<K>& p, int64_t tile, int T,
+                                                   const int64_t* a_split)
+{
+    const int64_t d0 = tile * T;
+    const int64_t d1 = d0 + T < p.total ? d0 + T : p.total;
+    const Pair<K> q = pair_at(p, d0);
+    const int64_t d0l = d0 - q.base, d1l = d1 - q.base;
+    const int64_t a0 = clamp_split(a_split[tile], d0l, q.na, q.nb);
+    int64_t a1 = (d1l == q.na + q.nb) ? q.na : clamp_split(a_split[tile + 1], d1l, q.na, q.nb);
+    a1 = a1 < a0 ? a0 : (a1 > a0 + (d1l - d0l) ? a0 + (d1l - d0l) : a1);
+    const int64_t b0 = d0l - a0, b1 = d1l - a1;
+    TilePlace<K> t;
+    t.gA = q.A + a0;
+    t.gB = q.B + b0;
+    t.gvA = q.AV ? q.AV + a0 : nullptr;
+    t.gvB = q.BV ? q.BV + b0 : nullptr;
+    t.la = (int)(a1 - a0);
+    t.lb = (int)(b1 - b0);
+    t.d0 = d0;
+    return t;
+}
+
+// Shared-memory view of a tile placed in a stage (keys at their 16-byte phase).
+template <class K, bool VALS, int NT, int VT>
+__device__ __forceinline__ TileView<K, VALS, NT, VT> stage_view(const TilePlace<K>& t, K* sk,
+                                                                uint32_t* sv, uint16_t* sidx)
+{
+    constexpr int EK = 16 / sizeof(K);
+    TileView<K, VALS, NT, VT> v;
+    v.la = t.la;
+    v.lb = t.lb;
+    v.sidx = sidx;
+    v.sA = sk + phase16(t.gA);
+    v.sB = sk + ((phase16(t.gA) + t.la + EK - 1) / EK) * EK + phase16(t.gB);
+    if constexpr (VALS) {
+        v.vA = sv + phase16(t.gvA);
+        v.vB = sv + ((phase16(t.gvA) + t.la + 3) / 4) * 4 + phase16(t.gvB);
+    } else {
+        v.vA = v.vB = nullptr;
+    }
+    return v;
+}
+
+// Issue the bulk copies of a window pair's aligned interiors (one thread).
+template <class E>
+__device__ __forceinline__ uint32_t interior_bytes(const E* g, int n)
+{
+    const int h = head_to_16(g, n);
+    return (uint32_t)(((n - h) * (int)sizeof(E)) & ~15);
+}
+
+template <class E>
+__device__ __forceinline__ void issue_interior(E* s, const E* g, int n, uint64_t* bar)
+{
+    const int h = head_to_16(g, n);
+    const uint32_t bytes = (uint32_t)(((n - h) * (int)sizeof(E)) & ~15);
+    if (bytes) bulk_g2s(s + h, g + h, bytes, bar);
+}
+
+// Edge elements of one window pair (outside the aligned interiors): at most
+// V-1 at each end of each window; thread slot j in [0, 4V) owns one.
+template <class E>
+struct EdgeLoad {
+    E val;
+    int dst;  // index relative to sA (j < 2V) or sB; -1 if none
+    bool in_b;
+};
+
+template <class E>
+__device__ __forceinline__ EdgeLoad<E> edge_load(int j, const E* gA, int la, const E* gB, int lb)
+{
+    constexpr int V = 16 / sizeof(E);
+    EdgeLoad<E> e;
+    e.dst = -1;
+    e.in_b = j >= 2 * V;
+    e.val = E(0);
+    const E* g = e.in_b ? gB : gA;
+    const int n = e.in_b ? lb : la;
+    const int h = head_to_16(g, n);
+    const int tail0 = h + ((n - h) / V) * V;
+    const int jj = j % (2 * V);
+    int idx = -1;
+    if (jj < V) {
+        if (jj < h) idx = jj;
+    } else if (tail0 + (jj - V) < n) {
+        idx = tail0 + (jj - V);
+    }
+    if (idx >= 0) {
+        e.val = __ldg(g + idx);
+        e.dst = idx;
+    }
+    return e;
+}
+
+template <class K, bool VALS, int NT, int VT>
+struct BulkSmem {
+    static constexpr int T = NT * VT;
+    static constexpr int EK = 16 / sizeof(K);
+    static constexpr size_t keys_bytes = ((size_t)(T + 3 * EK) * sizeof(K) + 15) / 16 * 16;
+    static constexpr size_t vals_bytes = VALS ? ((size_t)(T + 12) * 4 + 15) / 16 * 16 : 0;
+    static constexpr size_t stage_bytes = keys_bytes + vals_bytes;
+    static constexpr size_t idx_bytes = (size_t)T * 2;
+    static constexpr size_t bytes = 2 * stage_bytes + idx_bytes + 16;  // + two mbarriers
+};
+
+// Persistent, double-buffered tile loop.
+template <class K, bool VALS, int NT, int VT>
+__device__ __forceinline__ void merge_tiles_bulk(const TileArgs<K>& p, int64_t ntiles,
+                                                 const int64_t* a_split, unsigned char* smem,
+                                                 unsigned int* err)
+{
+    using SM = BulkSmem<K, VALS, NT, VT>;
+    constexpr int T = SM::T;
+    constexpr int EK = SM::EK;
+    constexpr uint32_t WAIT_LIMIT = 1u << 22;
+    const int tid = threadIdx.x;
+    K* sk[2];
+    uint32_t* sv[2];
+    for (int s = 0; s < 2; ++s) {
+        sk[s] = reinterpret_cast<K*>(smem + s * SM::stage_bytes);
+        sv[s] = reinterpret_cast<uint32_t*>(smem + s * SM::stage_bytes + SM::keys_bytes);
+    }
+    uint16_t* sidx = reinterpret_cast<uint16_t*>(smem + 2 * SM::stage_bytes);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * SM::stage_bytes + SM::idx_bytes);
+
+    int64_t tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    // Issue the loads of `t` into stage s: bulk interiors by thread 0, edge
+    // elements into registers by threads [0, 4EK) (keys) and [64, 64+16)
+    // (values), stored to shared memory later by put_edges().
+    auto issue = [&](const TilePlace<K>& t, int s) {
+        const auto v = stage_view<K, VALS, NT, VT>(t, sk[s], sv[s], sidx);
+        if (tid == 0) {
+            uint32_t tx = interior_bytes(t.gA, t.la) + interior_bytes(t.gB, t.lb);
+            if constexpr (VALS) tx += interior_bytes(t.gvA, t.la) + interior_bytes(t.gvB, t.lb);
+            mbar_arrive_expect_tx(&bar[s], tx);
+            issue_interior(v.sA, t.gA, t.la, &bar[s]);
+            issue_interior(v.sB, t.gB, t.lb, &bar[s]);
+            if constexpr (VALS) {
+                issue_interior(v.vA, t.gvA, t.la, &bar[s]);
+                issue_interior(v.vB, t.gvB, t.lb, &bar[s]);
+            }
+        }
+    };
+    EdgeLoad<K> ek;
+    EdgeLoad<uint32_t> ev;
+    ek.dst = ev.dst = -1;
+    auto load_edges = [&](const TilePlace<K>& t) {
+        ek.dst = ev.dst = -1;
+        if (tid < 4 * EK) ek = edge_load(tid, t.gA, t.la, t.gB, t.lb);
+        if constexpr (VALS) {
+            if (tid >= 64 && tid < 64 + 16) ev = edge_load(tid - 64, t.gvA, t.la, t.gvB, t.lb);
+        }
+    };
+    auto put_edges = [&](const TilePlace<K>& t, int s) {
+        const auto v = stage_view<K, VALS, NT, VT>(t, sk[s], sv[s], sidx);
+        if (ek.dst >= 0) (ek.in_b ? v.sB : v.sA)[ek.dst] = ek.val;
+        if constexpr (VALS) {
+            if (ev.dst >= 0) (ev.in_b ? v.vB : v.vA)[ev.dst] = ev.val;
+        }
+    };
+
+    TilePlace<K> cur = tile_place(p, tile, T, a_split);
+    issue(cur, 0);
+    load_edges(cur);
+    put_edges(cur, 0);
+    __syncthreads();
+    uint32_t phase[2] = {0, 0};
+    int s = 0;
+    for (;;) {
+        const int64_t next_tile = tile + gridDim.x;
+        const bool has_next = next_tile < ntiles;
+        TilePlace<K> nxt;
+        if (has_next) {
+            nxt = tile_place(p, next_tile, T, a_split);
+            issue(nxt, s ^ 1);
+            load_edges(nxt);
+        }
+        // Wait for this tile's interiors (bounded; all threads agree).
+        const bool ok = __syncthreads_and(mbar_wait_bounded(&bar[s], phase[s], WAIT_LIMIT));
+        if (!ok) {
+            if (tid == 0) atomicOr(err, MP_KERR_MBAR_TIMEOUT);
+            // Let copies still in flight land before the CTA leaves.
+            mbar_wait_bounded(&bar[s], phase[s], WAIT_LIMIT);
+            if (has_next) mbar_wait_bounded(&bar[s ^ 1], phase[s ^ 1], WAIT_LIMIT);
+            return;
+        }
+        phase[s] ^= 1;
+        const auto v = stage_view<K, VALS, NT, VT>(cur, sk[s], sv[s], sidx);
+        const int L = cur.la + cur.lb;
+        {
+            const int diag = tid * VT < L ? tid * VT : L;
+            const int ai = smem_diagonal_search(v.sA, cur.la, v.sB, cur.lb, diag, p.codec);
+            uint32_t packed[VT / 2];
+            serial_merge_indices<K, VT>(v.sA, cur.la, v.sB, cur.lb, ai, diag - ai, p.codec, packed);
+            put_indices<VT>(sidx, packed);
+        }
+        __syncthreads();
+        store_tile<K, VALS, NT, VT>(v, p.out + cur.d0, VALS ? p.outv + cur.d0 : nullptr);
+        if (has_next) put_edges(nxt, s ^ 1);
+        __syncthreads();
+        if (!has_next) break;
+        cur = nxt;
+        tile = next_tile;
+        s ^= 1;
+    }
+}
+
+}  // namespace mp

@@ -16,7 +16,9 @@ pytestmark = pytest.mark.gpu
 DTYPES = [np.int32, np.uint32, np.float32, np.uint64, np.int64]
 SIZES = [(0, 0), (1, 0), (0, 1), (1, 1), (5, 3), (4095, 1), (4096, 4096), (12_305, 8_209),
          (70_001, 33_333), (100_000, 0), (0, 65_537), (3, 200_000)]
-PLANS = [(128, 8), (256, 8), (128, 16), (256, 16), (512, 8)]
+PLANS = [(128, 8), (256, 8), (128, 16), (256, 16), (512, 8),
+         (128, 8, mp.MP_STAGE_BULK), (256, 8, mp.MP_STAGE_BULK), (128, 16, mp.MP_STAGE_BULK),
+         (256, 16, mp.MP_STAGE_BULK)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -77,8 +79,9 @@ def test_merge_every_plan(plan, dt):
         assert first_mismatch(to_host(ov, np.uint32), ev) is None
 
 
+@pytest.mark.parametrize("plan", [None, (128, 8, mp.MP_STAGE_BULK), (256, 16, mp.MP_STAGE_BULK)], ids=str)
 @pytest.mark.parametrize("dt", [np.int32, np.uint64, np.float32], ids=lambda d: np.dtype(d).name)
-def test_unaligned_pointers(dt):
+def test_unaligned_pointers(dt, plan):
     """Windows and outputs at every 16-byte phase: sub-views offset by one
     element exercise the scalar head/tail staging and the scalar store path."""
     rng = np.random.default_rng(400)
@@ -93,7 +96,7 @@ def test_unaligned_pointers(dt):
         BV = vals_to_dev(np.concatenate([np.zeros(off_b, np.uint32), bv]))[off_b:]
         OK = torch.empty(na + nb + off_o, dtype=A.dtype, device="cuda")[off_o:]
         OV = torch.empty(na + nb + off_o, dtype=torch.int32, device="cuda")[off_o:]
-        mp.mp_merge_pairs(A, AV, B, BV, OK, OV)
+        mp.mp_merge_plan(A, B, AV, BV, OK, OV, plan=plan)
         ek, ev = oracle.merge(a, b, av, bv)
         assert first_mismatch(to_host(OK, dt), ek) is None, (off_a, off_b, off_o)
         assert first_mismatch(to_host(OV, np.uint32), ev) is None, (off_a, off_b, off_o)
@@ -112,6 +115,27 @@ def test_partition_matches_oracle_split(dt):
         diags = [min(t * spacing, n) for t in range((n + spacing - 1) // spacing + 1)]
         expect = [oracle.split(a, b, d)[0] for d in diags]
         assert got.tolist() == expect
+
+
+@pytest.mark.parametrize("dt", DTYPES, ids=lambda d: np.dtype(d).name)
+def test_bulk_staging_edge_sizes(dt):
+    """TMA-staged persistent merge: empty sides, windows shorter than one
+    16-byte granule, many tiles per CTA (large inputs), and no kernel error
+    reported by its bounded waits."""
+    rng = np.random.default_rng(550)
+    for na, nb in [(1, 0), (0, 1), (1, 1), (3, 2), (5, 17), (4096, 1), (2_000_000, 1_500_001),
+                   (0, 300_001), (1_000_003, 0)]:
+        a, b = random_sorted(rng, dt, na, "ties"), random_sorted(rng, dt, nb, "ties")
+        av = np.arange(na, dtype=np.uint32)
+        bv = np.arange(na, na + nb, dtype=np.uint32)
+        for plan in [(128, 8, mp.MP_STAGE_BULK), (256, 16, mp.MP_STAGE_BULK)]:
+            ok, ov = mp.mp_merge_plan(to_dev(a), to_dev(b), vals_to_dev(av), vals_to_dev(bv), plan=plan)
+            ek, ev = oracle.merge(a, b, av, bv)
+            assert first_mismatch(to_host(ok, dt), ek) is None, (na, nb, plan)
+            assert first_mismatch(to_host(ov, np.uint32), ev) is None, (na, nb, plan)
+            ko = mp.mp_merge_plan(to_dev(a), to_dev(b), plan=plan)
+            assert first_mismatch(to_host(ko, dt), ek) is None, (na, nb, plan)
+    assert mp.mp_kernel_error(reset=True) == 0
 
 
 def test_merge_on_side_stream():
