@@ -303,6 +303,32 @@ MP_API mp_status mp_graph_destroy(mp_graph* graph);
  */
 MP_API mp_status mp_kernel_error(unsigned int* code, int reset);
 
+/*
+ * mp_merge_noalloc -- the merge of mp_merge_plan (values move when any value
+ * pointer is non-NULL) for callers that must not allocate device memory on
+ * the call path: code running inside another runtime's memory arena that
+ * already holds the device's memory, or latency-critical loops in which an
+ * allocation call may block or synchronise.  The paper has no counterpart;
+ * this is a deployment variant of Alg. 1.
+ *   It calls no cudaMalloc, cudaFree or allocating library routine: the
+ *   split points live in a fixed 2 MiB array compiled into the library
+ *   (262144 entries, tile of 4096 outputs, 256 threads x 16 items), which
+ *   every GPU that loads the library holds until the process exits.
+ *   na + nb may be at most 1073737728; larger sizes return
+ *   MP_ERR_INVALID_ARG before anything is enqueued.
+ *   The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress, no allocation) with that device current; make
+ *   that first call before any stream capture.
+ *   All calls share the one array: calls whose work overlaps on the GPU
+ *   (other streams, other host threads) race and must not be issued; calls
+ *   on one stream are ordered.  No part of the array needs to start at zero
+ *   (each call's partition kernel writes every entry its merge kernel reads).
+ */
+MP_API mp_status mp_merge_noalloc(mp_dtype dtype,
+                                  const void* a_keys, const uint32_t* a_vals, int64_t na,
+                                  const void* b_keys, const uint32_t* b_vals, int64_t nb,
+                                  void* out_keys, uint32_t* out_vals, mp_stream_t stream);
+
 /* One problem of mp_merge_grouped. */
 typedef struct mp_merge_desc {
     int32_t dtype;    /* mp_dtype of this problem's keys */

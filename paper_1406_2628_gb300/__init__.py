@@ -114,6 +114,7 @@ _SIGNATURES = {
     "mp_merge_grouped": ([ctypes.POINTER(mp_merge_desc), _I64, _I32, _P], _I32),
     "mp_clock_seconds": ([], ctypes.c_double),
     "mp_kernel_error": ([ctypes.POINTER(ctypes.c_uint), _I32], _I32),
+    "mp_merge_noalloc": ([_I32, _P, _P, _I64, _P, _P, _I64, _P, _P, _P], _I32),
     "mp_autotune_merge": ([_I32, _P, _P, _I64, _P, _P, _I64, _P, _P, _I32, ctypes.POINTER(mp_plan), _P], _I32),
     "mp_autotune_batched": ([_I32, _P, _P, _P, _P, _I64, _I64, _I64, _P, _P, _P, _P, _I32,
                              ctypes.POINTER(mp_plan), _P], _I32),
