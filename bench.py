@@ -172,6 +172,20 @@ class ClockSampler:
                 "power_w_max": max((num(r[4]) or 0) for r in busy)}
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of every rank's x (all ranks get it)."""
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(units_per_rank: int, ms: float, world: int) -> float:
+    """Whole-job rate in G units/s: every rank processed units_per_rank in at
+    most ms milliseconds (the max over ranks)."""
+    return units_per_rank * world / (ms * 1e-3) / 1e9
+
+
 def workload(args, seed_offset=0):
     import gen
     n_a, n_b = 1 << args.log2_a, 1 << args.log2_b
@@ -586,9 +600,7 @@ def run_ours(args):
         dist.barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
     if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
 
     # Per-kernel timing on the same stream: partition alone, merge alone.
     tile = mp.mp_merge_tile_items(torch.uint64, True, n, plan)
@@ -635,10 +647,8 @@ def run_ours(args):
             mp.mp_merge_pairs_host(hA, hAV, hB, hBV, hOK, hOV)
         e2e_s = (time.perf_counter() - t0) / args.e2e_steps
         if world > 1:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": n * world / e2e_s / 1e9, "unit": UNIT,
+            e2e_s = max_over_ranks(e2e_s, dist, dev)
+        e2e = {"value": weak_scaling_value(n, e2e_s * 1e3, world), "unit": UNIT,
                "h2d_bytes_per_step": int(a.nbytes + av.nbytes + b.nbytes + bv.nbytes),
                "d2h_bytes_per_step": int(n * 12), "ms_per_step": e2e_s * 1e3,
                "call": "mp_merge_pairs_host (pinned host buffers, copies in and out inside the call)"}
@@ -650,7 +660,7 @@ def run_ours(args):
     peak, peak_kind = measured_peak()
     alg_bytes = 2 * n * 12
     achieved = alg_bytes / (merge_ms * 1e-3) / 1e9
-    value = n * world / (ms * 1e-3) / 1e9
+    value = weak_scaling_value(n, ms, world)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
