@@ -47,7 +47,7 @@ UNIT = "Gkeys/s"
 NOMINAL_HBM_GBS = 7900.0
 PEAK_FALLBACK_GBS = 6800.0
 KERNEL_SOURCES = ["paper_1406_2628_gb300/csrc/merge.cu", "paper_1406_2628_gb300/csrc/mp_tile.cuh",
-                  "paper_1406_2628_gb300/csrc/mp_device.cuh"]
+                  "paper_1406_2628_gb300/csrc/mp_device.cuh", "paper_1406_2628_gb300/csrc/mp_bulk.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "merge_tile_kernel_large_kv_traffic.json")
 
 
@@ -666,7 +666,10 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": config_dict(args, world),
-        "roofline": {"bound": "hbm", "kernel": "merge_tile_kernel", "achieved": achieved,
+        "roofline": {"bound": "hbm", "kernel": "merge_tile_bulk_kernel (TMA-staged merge tiles)",
+                     "plan": {"block_threads": tile // (8 if tile == 2048 else 16) if plan is None else plan[0],
+                              "tile": tile},
+                     "achieved": achieved,
                      "peak": peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy)",
                      "unit": "GB/s", "frac": achieved / peak,
                      "frac_of_nominal_7900": achieved / NOMINAL_HBM_GBS,

@@ -38,23 +38,22 @@ __global__ void __launch_bounds__(256) partition_kernel(TileArgs<K> p, int64_t s
 // ---------------------------------------------------------------------------
 // Merge tile kernel: one CTA per tile of NT*VT outputs.
 // ---------------------------------------------------------------------------
-template <class K, bool VALS, int NT, int VT>
+template <class K, bool VALS, int NT, int VT, int CK>
 __global__ void __launch_bounds__(NT) merge_tile_kernel(TileArgs<K> p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     // Wait for the partition kernel (programmatic dependent launch).
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    merge_tile_body<K, VALS, NT, VT>(p, blockIdx.x, p.a_split, smem);
+    merge_tile_body<K, VALS, NT, VT, CK>(p, blockIdx.x, p.a_split, smem);
 }
 
-// Persistent variant: windows staged by TMA bulk copies, double-buffered.
-template <class K, bool VALS, int NT, int VT>
-__global__ void __launch_bounds__(NT) merge_tile_bulk_kernel(TileArgs<K> p, int64_t ntiles,
-                                                              unsigned int* err)
+// Variant whose windows are staged by TMA bulk copies (one tile per CTA).
+template <class K, bool VALS, int NT, int VT, int CK>
+__global__ void __launch_bounds__(NT) merge_tile_bulk_kernel(TileArgs<K> p, unsigned int* err)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    merge_tiles_bulk<K, VALS, NT, VT>(p, ntiles, p.a_split, smem, err);
+    merge_tile_bulk_body<K, VALS, NT, VT, CK>(p, blockIdx.x, p.a_split, smem, err);
 }
 
 // Device address of the kernel error word on the current device.
@@ -109,11 +108,11 @@ cudaError_t launch_partition(const MergeProblem& p, int64_t spacing, int64_t* a_
     return cudaGetLastError();
 }
 
-template <class K, bool VALS, int NT, int VT>
-static cudaError_t launch_tiles_t(const MergeProblem& p, const int64_t* a_split, cudaStream_t stream)
+template <class K, bool VALS, int NT, int VT, int CK>
+static cudaError_t launch_tiles_ck(const MergeProblem& p, const int64_t* a_split, cudaStream_t stream)
 {
     using SM = TileSmem<K, VALS, NT, VT>;
-    auto kern = merge_tile_kernel<K, VALS, NT, VT>;
+    auto kern = merge_tile_kernel<K, VALS, NT, VT, CK>;
     static bool configured = false;  // attribute is per function, set once
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -135,28 +134,31 @@ static cudaError_t launch_tiles_t(const MergeProblem& p, const int64_t* a_split,
     return cudaLaunchKernelEx(&cfg, kern, make_args<K>(p, a_split));
 }
 
+// Unsigned keys compare as they are; other dtypes go through the codec.
 template <class K, bool VALS, int NT, int VT>
-static cudaError_t launch_bulk_t(const MergeProblem& p, const int64_t* a_split, cudaStream_t stream)
+static cudaError_t launch_tiles_t(const MergeProblem& p, const int64_t* a_split, cudaStream_t stream)
+{
+    if (p.kind.flip == 0 && p.kind.fmask == 0)
+        return launch_tiles_ck<K, VALS, NT, VT, CODEC_IDENTITY>(p, a_split, stream);
+    return launch_tiles_ck<K, VALS, NT, VT, CODEC_RUNTIME>(p, a_split, stream);
+}
+
+template <class K, bool VALS, int NT, int VT, int CK>
+static cudaError_t launch_bulk_ck(const MergeProblem& p, const int64_t* a_split, cudaStream_t stream)
 {
     using SM = BulkSmem<K, VALS, NT, VT>;
-    auto kern = merge_tile_bulk_kernel<K, VALS, NT, VT>;
-    static int blocks_per_sm = 0;
-    static int num_sms = 0;
-    if (blocks_per_sm == 0) {
+    auto kern = merge_tile_bulk_kernel<K, VALS, NT, VT, CK>;
+    static bool configured = false;
+    if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
         if (e != cudaSuccess) return e;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, NT, SM::bytes);
-        if (e != cudaSuccess) return e;
-        if (blocks_per_sm < 1) blocks_per_sm = 1;
+        configured = true;
     }
+    unsigned int* err = kernel_error_word();
+    if (!err) return cudaErrorInvalidSymbol;
     const int64_t tiles = ceil_div(p.total(), (int64_t)NT * VT);
-    const int64_t grid = std::min<int64_t>(tiles, (int64_t)num_sms * blocks_per_sm);
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
+    cfg.gridDim = dim3((unsigned)tiles);
     cfg.blockDim = dim3(NT);
     cfg.dynamicSmemBytes = SM::bytes;
     cfg.stream = stream;
@@ -165,9 +167,15 @@ static cudaError_t launch_bulk_t(const MergeProblem& p, const int64_t* a_split, 
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    unsigned int* err = kernel_error_word();
-    if (!err) return cudaErrorInvalidSymbol;
-    return cudaLaunchKernelEx(&cfg, kern, make_args<K>(p, a_split), tiles, err);
+    return cudaLaunchKernelEx(&cfg, kern, make_args<K>(p, a_split), err);
+}
+
+template <class K, bool VALS, int NT, int VT>
+static cudaError_t launch_bulk_t(const MergeProblem& p, const int64_t* a_split, cudaStream_t stream)
+{
+    if (p.kind.flip == 0 && p.kind.fmask == 0)
+        return launch_bulk_ck<K, VALS, NT, VT, CODEC_IDENTITY>(p, a_split, stream);
+    return launch_bulk_ck<K, VALS, NT, VT, CODEC_RUNTIME>(p, a_split, stream);
 }
 
 // Compiled tile shapes (NT, VT): vector staging and TMA bulk staging.
@@ -205,14 +213,16 @@ Shape default_merge_shape(int key_bytes, bool with_values, int64_t total)
     Shape s;
     if (tuned_shape("merge", key_bytes, with_values, total, &s)) return s;
     // Shapes with the shortest partition + merge step on GB300 for large
-    // merges (tile-shape sweep); mp_autotune_merge overrides per size class.
-    s.staging = MP_STAGE_VECTOR;
+    // merges (tile-shape sweep): TMA-staged tiles throughout (they need no
+    // staging registers, so more CTAs stay resident);
+    // mp_autotune_merge overrides per size class.
+    s.staging = MP_STAGE_BULK;
     if (key_bytes == 8) {
         s.nt = with_values ? 256 : 128;
-        s.vt = 16;
+        s.vt = with_values ? 8 : 16;
     } else {
         s.nt = 256;
-        s.vt = 16;
+        s.vt = with_values ? 8 : 16;
     }
     return s;
 }

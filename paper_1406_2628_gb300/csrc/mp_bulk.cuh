@@ -1,13 +1,12 @@
-// mp_bulk.cuh -- persistent merge tiles staged by TMA bulk copies.
+// mp_bulk.cuh -- merge tiles staged by TMA bulk copies.
 //
 // Same Merge Path tile as mp_tile.cuh (one CTA-tile = one path segment,
 // Cor. 6; windows bounded by Lemma 16; per-thread splits by Thm 17), but the
 // windows are moved by the Tensor Memory Accelerator: one thread issues a
 // 1D bulk copy (cp.async.bulk) of each window's 16-byte-aligned interior,
 // completion is tracked by an mbarrier, and the ragged edges (< 16 bytes per
-// side) are loaded by a few threads.  Each CTA walks tiles blockIdx.x,
-// blockIdx.x + gridDim.x, ... with two shared-memory stages, so the bulk
-// copies of tile i+1 run while tile i is merged and stored.
+// side) are loaded by a few threads.  No thread holds staged data in
+// registers, so the tile needs fewer registers than the vector-staged one.
 #pragma once
 
 #include "mp_tile.cuh"
@@ -175,119 +174,73 @@ struct BulkSmem {
     static constexpr int EK = 16 / sizeof(K);
     static constexpr size_t keys_bytes = ((size_t)(T + 3 * EK) * sizeof(K) + 15) / 16 * 16;
     static constexpr size_t vals_bytes = VALS ? ((size_t)(T + 12) * 4 + 15) / 16 * 16 : 0;
-    static constexpr size_t stage_bytes = keys_bytes + vals_bytes;
-    static constexpr size_t idx_bytes = (size_t)T * 2;
-    static constexpr size_t bytes = 2 * stage_bytes + idx_bytes + 16;  // + two mbarriers
+    static constexpr size_t idx_bytes = ((size_t)T * 2 + 15) / 16 * 16;
+    static constexpr size_t bytes = keys_bytes + vals_bytes + idx_bytes + 16;  // + mbarrier
 };
 
-// Persistent, double-buffered tile loop.
-template <class K, bool VALS, int NT, int VT>
-__device__ __forceinline__ void merge_tiles_bulk(const TileArgs<K>& p, int64_t ntiles,
-                                                 const int64_t* a_split, unsigned char* smem,
-                                                 unsigned int* err)
+// One tile per CTA.
+template <class K, bool VALS, int NT, int VT, int CK>
+__device__ __forceinline__ void merge_tile_bulk_body(const TileArgs<K>& p, int64_t tile,
+                                                     const int64_t* a_split, unsigned char* smem,
+                                                     unsigned int* err)
 {
     using SM = BulkSmem<K, VALS, NT, VT>;
     constexpr int T = SM::T;
     constexpr int EK = SM::EK;
     constexpr uint32_t WAIT_LIMIT = 1u << 22;
     const int tid = threadIdx.x;
-    K* sk[2];
-    uint32_t* sv[2];
-    for (int s = 0; s < 2; ++s) {
-        sk[s] = reinterpret_cast<K*>(smem + s * SM::stage_bytes);
-        sv[s] = reinterpret_cast<uint32_t*>(smem + s * SM::stage_bytes + SM::keys_bytes);
-    }
-    uint16_t* sidx = reinterpret_cast<uint16_t*>(smem + 2 * SM::stage_bytes);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * SM::stage_bytes + SM::idx_bytes);
+    K* sk = reinterpret_cast<K*>(smem);
+    uint32_t* sv = reinterpret_cast<uint32_t*>(smem + SM::keys_bytes);
+    uint16_t* sidx = reinterpret_cast<uint16_t*>(smem + SM::keys_bytes + SM::vals_bytes);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::keys_bytes + SM::vals_bytes + SM::idx_bytes);
 
-    int64_t tile = blockIdx.x;
-    if (tile >= ntiles) return;
+    const TilePlace<K> t = tile_place(p, tile, T, a_split);
+    const auto v = stage_view<K, VALS, NT, VT>(t, sk, sv, sidx);
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        mbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-
-    // Issue the loads of `t` into stage s: bulk interiors by thread 0, edge
-    // elements into registers by threads [0, 4EK) (keys) and [64, 64+16)
-    // (values), stored to shared memory later by put_edges().
-    auto issue = [&](const TilePlace<K>& t, int s) {
-        const auto v = stage_view<K, VALS, NT, VT>(t, sk[s], sv[s], sidx);
-        if (tid == 0) {
-            uint32_t tx = interior_bytes(t.gA, t.la) + interior_bytes(t.gB, t.lb);
-            if constexpr (VALS) tx += interior_bytes(t.gvA, t.la) + interior_bytes(t.gvB, t.lb);
-            mbar_arrive_expect_tx(&bar[s], tx);
-            issue_interior(v.sA, t.gA, t.la, &bar[s]);
-            issue_interior(v.sB, t.gB, t.lb, &bar[s]);
-            if constexpr (VALS) {
-                issue_interior(v.vA, t.gvA, t.la, &bar[s]);
-                issue_interior(v.vB, t.gvB, t.lb, &bar[s]);
-            }
-        }
-    };
-    EdgeLoad<K> ek;
-    EdgeLoad<uint32_t> ev;
-    ek.dst = ev.dst = -1;
-    auto load_edges = [&](const TilePlace<K>& t) {
-        ek.dst = ev.dst = -1;
-        if (tid < 4 * EK) ek = edge_load(tid, t.gA, t.la, t.gB, t.lb);
+    if (tid == 0) {
+        uint32_t tx = interior_bytes(t.gA, t.la) + interior_bytes(t.gB, t.lb);
+        if constexpr (VALS) tx += interior_bytes(t.gvA, t.la) + interior_bytes(t.gvB, t.lb);
+        mbar_arrive_expect_tx(bar, tx);
+        issue_interior(v.sA, t.gA, t.la, bar);
+        issue_interior(v.sB, t.gB, t.lb, bar);
         if constexpr (VALS) {
-            if (tid >= 64 && tid < 64 + 16) ev = edge_load(tid - 64, t.gvA, t.la, t.gvB, t.lb);
+            issue_interior(v.vA, t.gvA, t.la, bar);
+            issue_interior(v.vB, t.gvB, t.lb, bar);
         }
-    };
-    auto put_edges = [&](const TilePlace<K>& t, int s) {
-        const auto v = stage_view<K, VALS, NT, VT>(t, sk[s], sv[s], sidx);
-        if (ek.dst >= 0) (ek.in_b ? v.sB : v.sA)[ek.dst] = ek.val;
-        if constexpr (VALS) {
-            if (ev.dst >= 0) (ev.in_b ? v.vB : v.vA)[ev.dst] = ev.val;
-        }
-    };
-
-    TilePlace<K> cur = tile_place(p, tile, T, a_split);
-    issue(cur, 0);
-    load_edges(cur);
-    put_edges(cur, 0);
-    __syncthreads();
-    uint32_t phase[2] = {0, 0};
-    int s = 0;
-    for (;;) {
-        const int64_t next_tile = tile + gridDim.x;
-        const bool has_next = next_tile < ntiles;
-        TilePlace<K> nxt;
-        if (has_next) {
-            nxt = tile_place(p, next_tile, T, a_split);
-            issue(nxt, s ^ 1);
-            load_edges(nxt);
-        }
-        // Wait for this tile's interiors (bounded; all threads agree).
-        const bool ok = __syncthreads_and(mbar_wait_bounded(&bar[s], phase[s], WAIT_LIMIT));
-        if (!ok) {
-            if (tid == 0) atomicOr(err, MP_KERR_MBAR_TIMEOUT);
-            // Let copies still in flight land before the CTA leaves.
-            mbar_wait_bounded(&bar[s], phase[s], WAIT_LIMIT);
-            if (has_next) mbar_wait_bounded(&bar[s ^ 1], phase[s ^ 1], WAIT_LIMIT);
-            return;
-        }
-        phase[s] ^= 1;
-        const auto v = stage_view<K, VALS, NT, VT>(cur, sk[s], sv[s], sidx);
-        const int L = cur.la + cur.lb;
-        {
-            const int diag = tid * VT < L ? tid * VT : L;
-            const int ai = smem_diagonal_search(v.sA, cur.la, v.sB, cur.lb, diag, p.codec);
-            uint32_t packed[VT / 2];
-            serial_merge_indices<K, VT>(v.sA, cur.la, v.sB, cur.lb, ai, diag - ai, p.codec, packed);
-            put_indices<VT>(sidx, packed);
-        }
-        __syncthreads();
-        store_tile<K, VALS, NT, VT>(v, p.out + cur.d0, VALS ? p.outv + cur.d0 : nullptr);
-        if (has_next) put_edges(nxt, s ^ 1);
-        __syncthreads();
-        if (!has_next) break;
-        cur = nxt;
-        tile = next_tile;
-        s ^= 1;
     }
+    // Ragged edges: threads [32, 32+4EK) for keys, [64, 80) for values.
+    if (tid >= 32 && tid < 32 + 4 * EK) {
+        const EdgeLoad<K> e = edge_load(tid - 32, t.gA, t.la, t.gB, t.lb);
+        if (e.dst >= 0) (e.in_b ? v.sB : v.sA)[e.dst] = e.val;
+    }
+    if constexpr (VALS) {
+        if (tid >= 64 && tid < 80) {
+            const EdgeLoad<uint32_t> e = edge_load(tid - 64, t.gvA, t.la, t.gvB, t.lb);
+            if (e.dst >= 0) (e.in_b ? v.vB : v.vA)[e.dst] = e.val;
+        }
+    }
+    // Every thread waits for the interiors itself (bounded), then the block
+    // agrees on the outcome; the barrier also publishes the edges.
+    const bool ok = __syncthreads_and(mbar_wait_bounded(bar, 0, WAIT_LIMIT));
+    if (!ok) {
+        if (tid == 0) atomicOr(err, MP_KERR_MBAR_TIMEOUT);
+        mbar_wait_bounded(bar, 0, WAIT_LIMIT);  // let copies in flight land
+        return;
+    }
+    const int L = t.la + t.lb;
+    {
+        const int diag = tid * VT < L ? tid * VT : L;
+        const int ai = smem_diagonal_search_ck<CK>(v.sA, t.la, v.sB, t.lb, diag, p.codec);
+        uint32_t packed[VT / 2];
+        serial_merge_indices_ck<K, VT, CK>(v.sA, t.la, v.sB, t.lb, ai, diag - ai, p.codec, packed);
+        put_indices<VT>(sidx, packed);
+    }
+    __syncthreads();
+    store_tile<K, VALS, NT, VT>(v, p.out + t.d0, VALS ? p.outv + t.d0 : nullptr);
 }
 
 }  // namespace mp

@@ -41,6 +41,21 @@ __device__ __forceinline__ K key_enc(K x, Codec<K> c)
     return x ^ ((fill & c.fmask) | c.flip);
 }
 
+// Codec kinds known at compile time: identity (unsigned keys: the
+// comparison needs no encoding at all) or the runtime flip/fmask codec.
+enum { CODEC_IDENTITY = 0, CODEC_RUNTIME = 1 };
+
+template <int CK, class K>
+__device__ __forceinline__ K key_enc_ck(K x, Codec<K> c)
+{
+    if constexpr (CK == CODEC_IDENTITY) {
+        (void)c;
+        return x;
+    } else {
+        return key_enc(x, c);
+    }
+}
+
 // Inverse of key_enc: the sign of the original is the complement of the
 // encoded top bit when fmask is set.
 template <class K>
@@ -259,6 +274,46 @@ __device__ __forceinline__ void serial_merge_indices(const K* sA, int la, const 
             packed[i / 2] = src;
         const K* nxt = take_a ? (sA + (ai < la ? ai + 1 : la)) : (sB + bi + 1);
         K kn = key_enc(*nxt, c);
+        if (take_a) { ka = kn; ++ai; }
+        else { kb = kn; ++bi; }
+    }
+}
+
+// Same diagonal search with a compile-time codec kind.
+template <int CK, class K>
+__device__ __forceinline__ int smem_diagonal_search_ck(const K* sA, int la, const K* sB, int lb,
+                                                       int diag, Codec<K> c)
+{
+    int lo = diag - lb > 0 ? diag - lb : 0;
+    int hi = diag < la ? diag : la;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (key_enc_ck<CK>(sA[mid], c) > key_enc_ck<CK>(sB[diag - 1 - mid], c))
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+// serial_merge_indices with a compile-time codec kind.
+template <class K, int VT, int CK>
+__device__ __forceinline__ void serial_merge_indices_ck(const K* sA, int la, const K* sB, int lb,
+                                                        int ai, int bi, Codec<K> c,
+                                                        uint32_t (&packed)[VT / 2])
+{
+    K ka = key_enc_ck<CK>(sA[ai], c);
+    K kb = key_enc_ck<CK>(sB[bi], c);
+#pragma unroll
+    for (int i = 0; i < VT; ++i) {
+        bool take_a = (bi >= lb) || (ai < la && !(ka > kb));
+        uint32_t src = take_a ? (uint32_t)ai : (uint32_t)(la + bi);
+        if (i & 1)
+            packed[i / 2] |= src << 16;
+        else
+            packed[i / 2] = src;
+        const K* nxt = take_a ? (sA + (ai < la ? ai + 1 : la)) : (sB + bi + 1);
+        K kn = key_enc_ck<CK>(*nxt, c);
         if (take_a) { ka = kn; ++ai; }
         else { kb = kn; ++bi; }
     }

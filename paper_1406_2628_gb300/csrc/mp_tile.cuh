@@ -227,7 +227,7 @@ __device__ __forceinline__ void store_tile(const TileView<K, VALS, NT, VT>& v, K
 
 // One tile of a merge problem (plain merge or sort pass): stage, split,
 // merge, store.  a_split holds the problem's split points at multiples of T.
-template <class K, bool VALS, int NT, int VT>
+template <class K, bool VALS, int NT, int VT, int CK = CODEC_RUNTIME>
 __device__ __forceinline__ void merge_tile_body(const TileArgs<K>& p, int64_t tile,
                                                 const int64_t* a_split, unsigned char* smem)
 {
@@ -255,9 +255,9 @@ __device__ __forceinline__ void merge_tile_body(const TileArgs<K>& p, int64_t ti
     // Per-thread split inside the window (Thm 17), then VT serial steps.
     {
         const int diag = tid * VT < L ? tid * VT : L;
-        const int ai = smem_diagonal_search(v.sA, la, v.sB, lb, diag, p.codec);
+        const int ai = smem_diagonal_search_ck<CK>(v.sA, la, v.sB, lb, diag, p.codec);
         uint32_t packed[VT / 2];
-        serial_merge_indices<K, VT>(v.sA, la, v.sB, lb, ai, diag - ai, p.codec, packed);
+        serial_merge_indices_ck<K, VT, CK>(v.sA, la, v.sB, lb, ai, diag - ai, p.codec, packed);
         put_indices<VT>(v.sidx, packed);
     }
     __syncthreads();

@@ -37,7 +37,7 @@ static Shape sort_merge_shape(int key_bytes)
     Shape s;
     s.nt = 256;
     s.vt = key_bytes == 8 ? 8 : 16;
-    s.staging = MP_STAGE_VECTOR;
+    s.staging = MP_STAGE_BULK;
     return s;
 }
 
