@@ -139,7 +139,12 @@ static mp_status resolve_shape(const KeyKind& k, bool vals, int64_t total, const
         if (plan->reserved != 0) return fail(MP_ERR_INVALID_ARG, "plan.reserved must be 0");
         if (plan->block_threads) s->nt = plan->block_threads;
         if (plan->items_per_thread) s->vt = plan->items_per_thread;
-        if (plan->staging) s->staging = plan->staging;
+        if (plan->staging) {
+            s->staging = plan->staging;
+        } else if (!merge_shape_supported(k.bytes, vals, *s)) {
+            // Automatic staging for a shape the default staging lacks.
+            s->staging = MP_STAGE_VECTOR;
+        }
     }
     if (!merge_shape_supported(k.bytes, vals, *s))
         return fail(MP_ERR_INVALID_ARG, "unsupported merge plan (block_threads, items_per_thread, staging)");

@@ -178,29 +178,46 @@ struct BulkSmem {
     static constexpr size_t bytes = keys_bytes + vals_bytes + idx_bytes + 16;  // + mbarrier
 };
 
-// One tile per CTA.
-template <class K, bool VALS, int NT, int VT, int CK>
-__device__ __forceinline__ void merge_tile_bulk_body(const TileArgs<K>& p, int64_t tile,
-                                                     const int64_t* a_split, unsigned char* smem,
-                                                     unsigned int* err)
-{
-    using SM = BulkSmem<K, VALS, NT, VT>;
-    constexpr int T = SM::T;
-    constexpr int EK = SM::EK;
-    constexpr uint32_t WAIT_LIMIT = 1u << 22;
-    const int tid = threadIdx.x;
-    K* sk = reinterpret_cast<K*>(smem);
-    uint32_t* sv = reinterpret_cast<uint32_t*>(smem + SM::keys_bytes);
-    uint16_t* sidx = reinterpret_cast<uint16_t*>(smem + SM::keys_bytes + SM::vals_bytes);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::keys_bytes + SM::vals_bytes + SM::idx_bytes);
+// Shared-memory regions of a TMA-staged tile.
+template <class K, bool VALS, int NT, int VT>
+struct BulkLayout {
+    K* sk;
+    uint32_t* sv;
+    uint16_t* sidx;
+    uint64_t* bar;
+    __device__ __forceinline__ explicit BulkLayout(unsigned char* smem)
+    {
+        using SM = BulkSmem<K, VALS, NT, VT>;
+        sk = reinterpret_cast<K*>(smem);
+        sv = reinterpret_cast<uint32_t*>(smem + SM::keys_bytes);
+        sidx = reinterpret_cast<uint16_t*>(smem + SM::keys_bytes + SM::vals_bytes);
+        bar = reinterpret_cast<uint64_t*>(smem + SM::keys_bytes + SM::vals_bytes + SM::idx_bytes);
+    }
+};
 
-    const TilePlace<K> t = tile_place(p, tile, T, a_split);
-    const auto v = stage_view<K, VALS, NT, VT>(t, sk, sv, sidx);
-    if (tid == 0) {
+// Initialise the CTA's mbarrier (one thread); the caller then synchronises.
+__device__ __forceinline__ void bulk_init(uint64_t* bar)
+{
+    if (threadIdx.x == 0) {
         mbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncthreads();
+}
+
+// Stage tile t into shared memory: thread 0 issues the bulk copies of the
+// aligned interiors, threads [32, 32+4EK) and [64, 80) copy the ragged
+// edges, every thread waits (bounded) for the mbarrier phase `parity`, and
+// the block agrees on the outcome (the barrier also publishes the edges).
+// Returns false, after recording MP_KERR_MBAR_TIMEOUT and giving copies in
+// flight a bounded time to land, if the wait ran out.  The caller must have
+// synchronised since the shared memory was last read.
+template <class K, bool VALS, int NT, int VT>
+__device__ __forceinline__ bool bulk_stage(const TilePlace<K>& t, const TileView<K, VALS, NT, VT>& v,
+                                           uint64_t* bar, uint32_t parity, unsigned int* err)
+{
+    constexpr int EK = 16 / sizeof(K);
+    constexpr uint32_t WAIT_LIMIT = 1u << 22;
+    const int tid = threadIdx.x;
     if (tid == 0) {
         uint32_t tx = interior_bytes(t.gA, t.la) + interior_bytes(t.gB, t.lb);
         if constexpr (VALS) tx += interior_bytes(t.gvA, t.la) + interior_bytes(t.gvB, t.lb);
@@ -212,7 +229,6 @@ __device__ __forceinline__ void merge_tile_bulk_body(const TileArgs<K>& p, int64
             issue_interior(v.vB, t.gvB, t.lb, bar);
         }
     }
-    // Ragged edges: threads [32, 32+4EK) for keys, [64, 80) for values.
     if (tid >= 32 && tid < 32 + 4 * EK) {
         const EdgeLoad<K> e = edge_load(tid - 32, t.gA, t.la, t.gB, t.lb);
         if (e.dst >= 0) (e.in_b ? v.sB : v.sA)[e.dst] = e.val;
@@ -223,21 +239,35 @@ __device__ __forceinline__ void merge_tile_bulk_body(const TileArgs<K>& p, int64
             if (e.dst >= 0) (e.in_b ? v.vB : v.vA)[e.dst] = e.val;
         }
     }
-    // Every thread waits for the interiors itself (bounded), then the block
-    // agrees on the outcome; the barrier also publishes the edges.
-    const bool ok = __syncthreads_and(mbar_wait_bounded(bar, 0, WAIT_LIMIT));
+    const bool ok = __syncthreads_and(mbar_wait_bounded(bar, parity, WAIT_LIMIT));
     if (!ok) {
         if (tid == 0) atomicOr(err, MP_KERR_MBAR_TIMEOUT);
-        mbar_wait_bounded(bar, 0, WAIT_LIMIT);  // let copies in flight land
-        return;
+        mbar_wait_bounded(bar, parity, WAIT_LIMIT);
     }
+    return ok;
+}
+
+// One tile of a merge problem (plain merge or sort pass) per CTA.
+template <class K, bool VALS, int NT, int VT, int CK>
+__device__ __forceinline__ void merge_tile_bulk_body(const TileArgs<K>& p, int64_t tile,
+                                                     const int64_t* a_split, unsigned char* smem,
+                                                     unsigned int* err)
+{
+    constexpr int T = NT * VT;
+    const int tid = threadIdx.x;
+    const BulkLayout<K, VALS, NT, VT> lay(smem);
+    const TilePlace<K> t = tile_place(p, tile, T, a_split);
+    const auto v = stage_view<K, VALS, NT, VT>(t, lay.sk, lay.sv, lay.sidx);
+    bulk_init(lay.bar);
+    __syncthreads();
+    if (!bulk_stage<K, VALS, NT, VT>(t, v, lay.bar, 0, err)) return;
     const int L = t.la + t.lb;
     {
         const int diag = tid * VT < L ? tid * VT : L;
         const int ai = smem_diagonal_search_ck<CK>(v.sA, t.la, v.sB, t.lb, diag, p.codec);
         uint32_t packed[VT / 2];
         serial_merge_indices_ck<K, VT, CK>(v.sA, t.la, v.sB, t.lb, ai, diag - ai, p.codec, packed);
-        put_indices<VT>(sidx, packed);
+        put_indices<VT>(lay.sidx, packed);
     }
     __syncthreads();
     store_tile<K, VALS, NT, VT>(v, p.out + t.d0, VALS ? p.outv + t.d0 : nullptr);
