@@ -20,6 +20,7 @@
 #include "mp_device.cuh"
 #include "mp_internal.h"
 #include "mp_tile.cuh"
+#include "mp_bulk.cuh"
 
 namespace mp {
 
@@ -87,97 +88,152 @@ __global__ void __launch_bounds__(256) batched_partition_kernel(BatchArgs<K> p, 
     asm volatile("griddepcontrol.launch_dependents;");
 }
 
+// The tile's window bounds (split points clamped into the grid and made
+// monotone, see merge_tile_body) and segment range.
+struct BatchTile {
+    int64_t d0, a0, a1, b0, b1, s0, s1;
+    int la, lb;
+};
+
+template <class K>
+__device__ __forceinline__ BatchTile batch_tile(const BatchArgs<K>& p, int64_t tile, int T)
+{
+    BatchTile t;
+    t.d0 = tile * T;
+    const int64_t d1 = t.d0 + T < p.total ? t.d0 + T : p.total;
+    t.a0 = clamp_split(p.a_split[tile], t.d0, p.na, p.nb);
+    int64_t a1 = clamp_split(p.a_split[tile + 1], d1, p.na, p.nb);
+    t.a1 = a1 < t.a0 ? t.a0 : (a1 > t.a0 + (d1 - t.d0) ? t.a0 + (d1 - t.d0) : a1);
+    t.b0 = t.d0 - t.a0;
+    t.b1 = d1 - t.a1;
+    int64_t s0 = p.seg_split[tile], s1 = p.seg_split[tile + 1];
+    t.s0 = s0 < 0 ? 0 : (s0 > p.nseg - 1 ? p.nseg - 1 : s0);
+    t.s1 = s1 < t.s0 ? t.s0 : (s1 > p.nseg - 1 ? p.nseg - 1 : s1);
+    t.la = (int)(t.a1 - t.a0);
+    t.lb = (int)(t.b1 - t.b0);
+    return t;
+}
+
+// Per-thread part of a batched tile: find the thread's segment and its
+// split inside the staged window, merge VT outputs (stepping to the next
+// segment when both sides of the current one are used up) and record the
+// outputs' sources.
+template <class K, bool VALS, int NT, int VT>
+__device__ __forceinline__ void batched_thread_merge(const BatchArgs<K>& p, const BatchTile& bt,
+                                                     const TileView<K, VALS, NT, VT>& v)
+{
+    const Codec<K> c = p.codec;
+    const int tid = threadIdx.x;
+    const int la = bt.la, lb = bt.lb, L = la + lb;
+    const int64_t a0 = bt.a0, a1 = bt.a1, b0 = bt.b0, b1 = bt.b1;
+    const int diag = tid * VT < L ? tid * VT : L;
+    if (diag >= L) return;
+    uint32_t packed[VT / 2];
+    const int64_t dg = bt.d0 + diag;
+    int64_t s = segment_of(p.a_off, p.b_off, bt.s0, bt.s1, dg);
+    const int64_t aS = __ldg(p.a_off + s), aE = __ldg(p.a_off + s + 1);
+    const int64_t bS = __ldg(p.b_off + s), bE = __ldg(p.b_off + s + 1);
+    const int64_t dl = dg - aS - bS;
+    // Alg. 2 inside segment s, restricted to the staged window (the split at
+    // dg lies between the tile's own splits).
+    int64_t lo = dl - (bE - bS);
+    lo = lo > 0 ? lo : 0;
+    lo = lo > a0 - aS ? lo : a0 - aS;
+    lo = lo > dl - (b1 - bS) ? lo : dl - (b1 - bS);
+    int64_t hi = dl < aE - aS ? dl : aE - aS;
+    hi = hi < a1 - aS ? hi : a1 - aS;
+    hi = hi < dl - (b0 - bS) ? hi : dl - (b0 - bS);
+    const K* sAs = v.sA + (aS - a0);  // segment s's A, window-relative
+    const K* sBs = v.sB + (bS - b0);
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (key_enc(sAs[mid], c) > key_enc(sBs[dl - 1 - mid], c))
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    // Window-relative positions, kept inside the window even for malformed
+    // offsets (no effect on valid input).
+    auto clampi = [](int64_t x, int top) { return (int)(x < 0 ? 0 : (x > top ? top : x)); };
+    int ai = clampi(aS + lo - a0, la);
+    int bi = clampi(bS + dl - lo - b0, lb);
+    int aEnd = clampi((aE < a1 ? aE : a1) - a0, la);
+    int bEnd = clampi((bE < b1 ? bE : b1) - b0, lb);
+    K ka = key_enc(v.sA[ai], c);
+    K kb = key_enc(v.sB[bi], c);
+#pragma unroll
+    for (int i = 0; i < VT; ++i) {
+        uint32_t src = 0;
+        if (diag + i < L) {
+            // Both sides of segment s used up: step to the next segment
+            // (skipping empty ones); ai, bi already point at its first elements.
+            while (ai >= aEnd && bi >= bEnd && s + 1 < p.nseg) {
+                ++s;
+                const int64_t na1 = __ldg(p.a_off + s + 1), nb1 = __ldg(p.b_off + s + 1);
+                aEnd = clampi((na1 < a1 ? na1 : a1) - a0, la);
+                bEnd = clampi((nb1 < b1 ? nb1 : b1) - b0, lb);
+            }
+            const bool take_a = ai < aEnd && (bi >= bEnd || !(ka > kb));
+            src = take_a ? (uint32_t)ai : (uint32_t)(la + bi);
+            const K* nxt = take_a ? (v.sA + (ai < la ? ai + 1 : la)) : (v.sB + (bi < lb ? bi + 1 : lb));
+            const K kn = key_enc(*nxt, c);
+            if (take_a) { ka = kn; ++ai; }
+            else { kb = kn; ++bi; }
+        }
+        if (i & 1)
+            packed[i / 2] |= src << 16;
+        else
+            packed[i / 2] = src;
+    }
+    put_indices<VT>(v.sidx, packed);
+}
+
 template <class K, bool VALS, int NT, int VT>
 __global__ void __launch_bounds__(NT) batched_merge_kernel(BatchArgs<K> p)
 {
     static_assert(VT % 4 == 0, "VT must be a multiple of 4");
     constexpr int T = NT * VT;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int tid = threadIdx.x;
-    const Codec<K> c = p.codec;
-
     asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int64_t tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
-        const int64_t d0 = tile * T;
-        const int64_t d1 = d0 + T < p.total ? d0 + T : p.total;
-        // Clamped into the grid and monotone (see merge_tile_kernel).
-        const int64_t a0 = clamp_split(p.a_split[tile], d0, p.na, p.nb);
-        int64_t a1 = clamp_split(p.a_split[tile + 1], d1, p.na, p.nb);
-        a1 = a1 < a0 ? a0 : (a1 > a0 + (d1 - d0) ? a0 + (d1 - d0) : a1);
-        const int64_t b0 = d0 - a0, b1 = d1 - a1;
-        int64_t s0 = p.seg_split[tile], s1 = p.seg_split[tile + 1];
-        s0 = s0 < 0 ? 0 : (s0 > p.nseg - 1 ? p.nseg - 1 : s0);
-        s1 = s1 < s0 ? s0 : (s1 > p.nseg - 1 ? p.nseg - 1 : s1);
-        const int la = (int)(a1 - a0), lb = (int)(b1 - b0);
-        const int L = la + lb;
-
-        const auto v = stage_tile<K, VALS, NT, VT>(smem, p.a + a0, la, p.b + b0, lb,
-                                                   VALS ? p.av + a0 : nullptr,
-                                                   VALS ? p.bv + b0 : nullptr);
-        const int diag = tid * VT < L ? tid * VT : L;
-        uint32_t packed[VT / 2];
-        if (diag < L) {
-            const int64_t dg = d0 + diag;
-            int64_t s = segment_of(p.a_off, p.b_off, s0, s1, dg);
-            const int64_t aS = __ldg(p.a_off + s), aE = __ldg(p.a_off + s + 1);
-            const int64_t bS = __ldg(p.b_off + s), bE = __ldg(p.b_off + s + 1);
-            const int64_t dl = dg - aS - bS;
-            // Alg. 2 inside segment s, restricted to the staged window (the
-            // split at dg lies between the tile's own splits).
-            int64_t lo = dl - (bE - bS);
-            lo = lo > 0 ? lo : 0;
-            lo = lo > a0 - aS ? lo : a0 - aS;
-            lo = lo > dl - (b1 - bS) ? lo : dl - (b1 - bS);
-            int64_t hi = dl < aE - aS ? dl : aE - aS;
-            hi = hi < a1 - aS ? hi : a1 - aS;
-            hi = hi < dl - (b0 - bS) ? hi : dl - (b0 - bS);
-            const K* sAs = v.sA + (aS - a0);  // segment s's A, window-relative
-            const K* sBs = v.sB + (bS - b0);
-            while (lo < hi) {
-                const int64_t mid = (lo + hi) >> 1;
-                if (key_enc(sAs[mid], c) > key_enc(sBs[dl - 1 - mid], c))
-                    hi = mid;
-                else
-                    lo = mid + 1;
-            }
-            // Window-relative positions, kept inside the window even for
-            // malformed offsets (no effect on valid input).
-            auto clampi = [](int64_t x, int hi) { return (int)(x < 0 ? 0 : (x > hi ? hi : x)); };
-            int ai = clampi(aS + lo - a0, la);
-            int bi = clampi(bS + dl - lo - b0, lb);
-            int aEnd = clampi((aE < a1 ? aE : a1) - a0, la);
-            int bEnd = clampi((bE < b1 ? bE : b1) - b0, lb);
-            K ka = key_enc(v.sA[ai], c);
-            K kb = key_enc(v.sB[bi], c);
-#pragma unroll
-            for (int i = 0; i < VT; ++i) {
-                uint32_t src = 0;
-                if (diag + i < L) {
-                    // Both sides of segment s used up: step to the next
-                    // segment (skipping empty ones); ai, bi already point at
-                    // its first elements.
-                    while (ai >= aEnd && bi >= bEnd && s + 1 < p.nseg) {
-                        ++s;
-                        const int64_t na1 = __ldg(p.a_off + s + 1), nb1 = __ldg(p.b_off + s + 1);
-                        aEnd = clampi((na1 < a1 ? na1 : a1) - a0, la);
-                        bEnd = clampi((nb1 < b1 ? nb1 : b1) - b0, lb);
-                    }
-                    const bool take_a = ai < aEnd && (bi >= bEnd || !(ka > kb));
-                    src = take_a ? (uint32_t)ai : (uint32_t)(la + bi);
-                    const K* nxt = take_a ? (v.sA + (ai < la ? ai + 1 : la)) : (v.sB + (bi < lb ? bi + 1 : lb));
-                    const K kn = key_enc(*nxt, c);
-                    if (take_a) { ka = kn; ++ai; }
-                    else { kb = kn; ++bi; }
-                }
-                if (i & 1)
-                    packed[i / 2] |= src << 16;
-                else
-                    packed[i / 2] = src;
-            }
-            put_indices<VT>(v.sidx, packed);
-        }
+        const BatchTile bt = batch_tile(p, tile, T);
+        const auto v = stage_tile<K, VALS, NT, VT>(smem, p.a + bt.a0, bt.la, p.b + bt.b0, bt.lb,
+                                                   VALS ? p.av + bt.a0 : nullptr,
+                                                   VALS ? p.bv + bt.b0 : nullptr);
+        batched_thread_merge<K, VALS, NT, VT>(p, bt, v);
         __syncthreads();
-        store_tile<K, VALS, NT, VT>(v, p.out + d0, VALS ? p.outv + d0 : nullptr);
+        store_tile<K, VALS, NT, VT>(v, p.out + bt.d0, VALS ? p.outv + bt.d0 : nullptr);
+        __syncthreads();
+    }
+}
+
+// Same, with the windows staged by TMA bulk copies (no staging registers).
+template <class K, bool VALS, int NT, int VT>
+__global__ void __launch_bounds__(NT) batched_merge_bulk_kernel(BatchArgs<K> p, unsigned int* err)
+{
+    constexpr int T = NT * VT;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const BulkLayout<K, VALS, NT, VT> lay(smem);
+    bulk_init(lay.bar);
+    __syncthreads();
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    uint32_t parity = 0;
+    for (int64_t tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
+        const BatchTile bt = batch_tile(p, tile, T);
+        TilePlace<K> t;
+        t.gA = p.a + bt.a0;
+        t.gB = p.b + bt.b0;
+        t.gvA = VALS ? p.av + bt.a0 : nullptr;
+        t.gvB = VALS ? p.bv + bt.b0 : nullptr;
+        t.la = bt.la;
+        t.lb = bt.lb;
+        t.d0 = bt.d0;
+        const auto v = stage_view<K, VALS, NT, VT>(t, lay.sk, lay.sv, lay.sidx);
+        if (!bulk_stage<K, VALS, NT, VT>(t, v, lay.bar, parity, err)) return;
+        parity ^= 1;
+        batched_thread_merge<K, VALS, NT, VT>(p, bt, v);
+        __syncthreads();
+        store_tile<K, VALS, NT, VT>(v, p.out + bt.d0, VALS ? p.outv + bt.d0 : nullptr);
         __syncthreads();
     }
 }
@@ -210,22 +266,26 @@ static BatchArgs<K> make_batch_args(const BatchedProblem& q, int64_t tile, const
     return p;
 }
 
-template <class K, bool VALS, int NT, int VT>
+template <class K, bool VALS, int NT, int VT, bool BULK>
 static cudaError_t launch_batched_t(const BatchedProblem& q, int64_t* a_split, int64_t* seg_split,
                                     cudaStream_t stream)
 {
-    using SM = TileSmem<K, VALS, NT, VT>;
-    auto kern = batched_merge_kernel<K, VALS, NT, VT>;
+    using SM = typename std::conditional<BULK, BulkSmem<K, VALS, NT, VT>, TileSmem<K, VALS, NT, VT>>::type;
+    auto kern = BULK ? (void (*)(BatchArgs<K>, unsigned int*))batched_merge_bulk_kernel<K, VALS, NT, VT>
+                     : nullptr;
+    auto kern_v = batched_merge_kernel<K, VALS, NT, VT>;
     static int blocks_per_sm = 0;
     static int num_sms = 0;
     if (blocks_per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
+        cudaError_t e = BULK ? cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes)
+                             : cudaFuncSetAttribute(kern_v, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
         if (e != cudaSuccess) return e;
         int dev = 0;
         cudaGetDevice(&dev);
         e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, NT, SM::bytes);
+        e = BULK ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, NT, SM::bytes)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern_v, NT, SM::bytes);
         if (e != cudaSuccess) return e;
         if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
@@ -247,14 +307,20 @@ static cudaError_t launch_batched_t(const BatchedProblem& q, int64_t* a_split, i
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, p);
+    if constexpr (BULK) {
+        unsigned int* err = kernel_error_word();
+        if (!err) return cudaErrorInvalidSymbol;
+        return cudaLaunchKernelEx(&cfg, kern, p, err);
+    } else {
+        return cudaLaunchKernelEx(&cfg, kern_v, p);
+    }
 }
 
 #define MP_BATCHED_SHAPES(X) X(128, 8) X(256, 8) X(128, 16) X(256, 16)
 
 static bool batched_shape_supported(const Shape& s)
 {
-    if (s.staging != MP_STAGE_VECTOR) return false;
+    if (s.staging != MP_STAGE_VECTOR && s.staging != MP_STAGE_BULK) return false;
 #define X(NT_, VT_) if (s.nt == NT_ && s.vt == VT_) return true;
     MP_BATCHED_SHAPES(X)
 #undef X
@@ -265,13 +331,21 @@ static cudaError_t launch_batched(const BatchedProblem& q, const Shape& s, int64
                                   int64_t* seg_split, cudaStream_t stream)
 {
     const bool vals = q.vals;
-#define X(NT_, VT_)                                                                            \
-    if (s.nt == NT_ && s.vt == VT_) {                                                          \
-        if (q.kind.bytes == 4)                                                                 \
-            return vals ? launch_batched_t<uint32_t, true, NT_, VT_>(q, a_split, seg_split, stream)   \
-                        : launch_batched_t<uint32_t, false, NT_, VT_>(q, a_split, seg_split, stream); \
-        return vals ? launch_batched_t<uint64_t, true, NT_, VT_>(q, a_split, seg_split, stream)       \
-                    : launch_batched_t<uint64_t, false, NT_, VT_>(q, a_split, seg_split, stream);     \
+    const bool bulk = s.staging == MP_STAGE_BULK;
+#define X(NT_, VT_)                                                                                    \
+    if (s.nt == NT_ && s.vt == VT_) {                                                                  \
+        if (q.kind.bytes == 4) {                                                                       \
+            if (bulk)                                                                                  \
+                return vals ? launch_batched_t<uint32_t, true, NT_, VT_, true>(q, a_split, seg_split, stream)   \
+                            : launch_batched_t<uint32_t, false, NT_, VT_, true>(q, a_split, seg_split, stream); \
+            return vals ? launch_batched_t<uint32_t, true, NT_, VT_, false>(q, a_split, seg_split, stream)      \
+                        : launch_batched_t<uint32_t, false, NT_, VT_, false>(q, a_split, seg_split, stream);    \
+        }                                                                                              \
+        if (bulk)                                                                                      \
+            return vals ? launch_batched_t<uint64_t, true, NT_, VT_, true>(q, a_split, seg_split, stream)       \
+                        : launch_batched_t<uint64_t, false, NT_, VT_, true>(q, a_split, seg_split, stream);     \
+        return vals ? launch_batched_t<uint64_t, true, NT_, VT_, false>(q, a_split, seg_split, stream)          \
+                    : launch_batched_t<uint64_t, false, NT_, VT_, false>(q, a_split, seg_split, stream);        \
     }
     MP_BATCHED_SHAPES(X)
 #undef X
@@ -305,8 +379,8 @@ mp_status batched_prepare(mp_dtype dtype, const void* a, const int64_t* a_off, c
 
     if (!tuned_shape("batched", k.bytes, vals, na_total + nb_total, s)) {
         s->nt = 256;
-        s->vt = k.bytes == 8 ? 8 : 16;
-        s->staging = MP_STAGE_VECTOR;
+        s->vt = (k.bytes == 8 || vals) ? 8 : 16;
+        s->staging = MP_STAGE_BULK;
     }
     if (plan) {
         if (plan->reserved) return fail(MP_ERR_INVALID_ARG, "plan.reserved must be 0");
@@ -348,7 +422,7 @@ cudaError_t batched_launch(const BatchedProblem& q, const Shape& s, void* scratc
 std::vector<Shape> batched_shapes()
 {
     std::vector<Shape> v;
-#define X(NT_, VT_) v.push_back(Shape{NT_, VT_, MP_STAGE_VECTOR});
+#define X(NT_, VT_) v.push_back(Shape{NT_, VT_, MP_STAGE_VECTOR}); v.push_back(Shape{NT_, VT_, MP_STAGE_BULK});
     MP_BATCHED_SHAPES(X)
 #undef X
     return v;

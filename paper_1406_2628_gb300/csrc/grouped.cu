@@ -17,6 +17,7 @@
 #include "mp_internal.h"
 #include "mp_sort.cuh"
 #include "mp_tile.cuh"
+#include "mp_bulk.cuh"
 
 namespace mp {
 
@@ -72,10 +73,11 @@ __global__ void __launch_bounds__(256) grouped_partition_kernel(const GroupMerge
     asm volatile("griddepcontrol.launch_dependents;");
 }
 
+// One tile of problem p per CTA, windows staged by TMA bulk copies.
 template <class K, bool VALS, int NT, int VT>
-__global__ void __launch_bounds__(NT) grouped_merge_kernel(const GroupMergeDesc* descs,
-                                                           const int64_t* tile_first, int nprob,
-                                                           const int64_t* splits)
+__global__ void __launch_bounds__(NT) grouped_merge_bulk_kernel(const GroupMergeDesc* descs,
+                                                                const int64_t* tile_first, int nprob,
+                                                                const int64_t* splits, unsigned int* err)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -83,7 +85,7 @@ __global__ void __launch_bounds__(NT) grouped_merge_kernel(const GroupMergeDesc*
     const int p = problem_of(tile_first, nprob, tile);
     const TileArgs<K> a = tile_args_of<K>(descs[p]);
     const int64_t first = __ldg(tile_first + p);
-    merge_tile_body<K, VALS, NT, VT>(a, tile - first, splits + first + p, smem);
+    merge_tile_bulk_body<K, VALS, NT, VT, CODEC_RUNTIME>(a, tile - first, splits + first + p, smem, err);
 }
 
 template <class K, bool VALS, int NT, int VT>
@@ -109,14 +111,16 @@ static cudaError_t launch_grouped_merge_t(const GroupMergeDesc* d_descs, const i
                                           const int64_t* d_bound_first, int nprob,
                                           int64_t total_tiles, int64_t* d_splits, cudaStream_t stream)
 {
-    using SM = TileSmem<K, VALS, NT, VT>;
-    auto kern = grouped_merge_kernel<K, VALS, NT, VT>;
+    using SM = BulkSmem<K, VALS, NT, VT>;
+    auto kern = grouped_merge_bulk_kernel<K, VALS, NT, VT>;
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
         if (e != cudaSuccess) return e;
         configured = true;
     }
+    unsigned int* err = kernel_error_word();
+    if (!err) return cudaErrorInvalidSymbol;
     const int64_t n_slots = total_tiles + nprob;
     grouped_partition_kernel<K><<<(unsigned)ceil_div(n_slots, 256), 256, 0, stream>>>(
         d_descs, d_bound_first, nprob, n_slots, (int64_t)NT * VT, d_splits);
@@ -132,7 +136,7 @@ static cudaError_t launch_grouped_merge_t(const GroupMergeDesc* d_descs, const i
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, d_descs, d_tile_first, nprob, (const int64_t*)d_splits);
+    return cudaLaunchKernelEx(&cfg, kern, d_descs, d_tile_first, nprob, (const int64_t*)d_splits, err);
 }
 
 // Grouped shapes: the default merge shapes of each key width.
@@ -145,6 +149,8 @@ cudaError_t launch_grouped_merge(int key_bytes, bool vals, const GroupMergeDesc*
                                  cudaStream_t stream)
 {
     if (nprob <= 0) return cudaSuccess;
+    // TMA-staged tiles: 4-byte keys 256 x 16 (tile 4096, = the block-sort
+    // tile, so sort passes pair whole runs), 8-byte keys 256 x 8 (2048).
     if (key_bytes == 4)
         return vals ? launch_grouped_merge_t<uint32_t, true, 256, 16>(d_descs, d_tile_first, d_bound_first, nprob, total_tiles, d_splits, stream)
                     : launch_grouped_merge_t<uint32_t, false, 256, 16>(d_descs, d_tile_first, d_bound_first, nprob, total_tiles, d_splits, stream);

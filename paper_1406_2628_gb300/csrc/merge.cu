@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(NT) merge_tile_bulk_kernel(TileArgs<K> p, unsi
 }
 
 // Device address of the kernel error word on the current device.
-static unsigned int* kernel_error_word()
+unsigned int* kernel_error_word()
 {
     static unsigned int* addr[64] = {};
     int dev = 0;

@@ -132,6 +132,9 @@ mp_status check_merge_args_ext(const KeyKind& k, const void* a, const uint32_t* 
                                const void* b, const uint32_t* bv, int64_t nb, const void* out,
                                const uint32_t* outv, bool vals, const char* fn);
 
+// Device address of the word kernels set when a bounded wait runs out.
+unsigned int* kernel_error_word();
+
 // Errors: record a detail for mp_last_error() and return the status.
 mp_status fail(mp_status st, const std::string& detail);
 mp_status cuda_fail(cudaError_t err, const char* where);
