@@ -1,28 +1,105 @@
 // mp_sort.cuh -- the block sort of one tile (first stage of the merge sort).
+//
+// Sec. I / Sec. III: each core first sorts its share on its own, then rounds
+// of merges follow.  Here one CTA sorts one tile of T = NT * VT keys:
+//   1. coalesced load into shared memory (keys encoded to unsigned order);
+//   2. each thread sorts its VT keys in registers with Batcher's odd-even
+//      merge network (stable: when values move, keys are compared together
+//      with their source positions, which are distinct);
+//   3. log2(NT) rounds of Merge Path inside shared memory: runs of width w
+//      merge pairwise, each thread producing VT outputs of its pair after a
+//      diagonal search (Alg. 2) in that pair;
+//   4. coalesced store (keys decoded; values gathered by source position).
+// Shared arrays are padded by one element per 128 bytes, so the
+// thread-major accesses (thread t touching elements t*VT .. t*VT+VT-1) and
+// the strided reads of the merge rounds spread over the banks.
 #pragma once
 
 #include "mp_device.cuh"
 
 namespace mp {
 
+// Padded position of element i of a shared array of E-byte elements.
+template <class E>
+__device__ __forceinline__ int padded(int i)
+{
+    return i + (i >> (sizeof(E) == 8 ? 4 : (sizeof(E) == 4 ? 5 : 6)));
+}
+
 template <class K, bool VALS, int NT, int VT>
 struct SortSmem {
     static constexpr int T = NT * VT;
-    static constexpr size_t keys_bytes = ((size_t)T * sizeof(K) + 15) / 16 * 16;
-    static constexpr size_t tags_bytes = ((size_t)T * 2 + 15) / 16 * 16;
+    static constexpr int KEYS = T + T / (sizeof(K) == 8 ? 16 : 32) + 1;
+    static constexpr int TAGS = VALS ? T + T / 64 + 2 : 0;
+    static constexpr size_t keys_bytes = ((size_t)KEYS * sizeof(K) + 15) / 16 * 16;
+    static constexpr size_t tags_bytes = ((size_t)TAGS * 2 + 15) / 16 * 16;
     static constexpr size_t vals_bytes = VALS ? (size_t)T * 4 : 0;
     static constexpr size_t bytes = keys_bytes + tags_bytes + vals_bytes;
 };
 
-// Sorts tile `tile` of in[0..n) into out (out may equal in: a CTA reads
-// its whole tile before writing).  Keys are encoded once on load, compared
-// as unsigned, and decoded on store; tags (tile-local source positions) ride
-// along so values can be gathered at the end.
+// Compare-exchange of register slots a < b: order by key, then (with
+// values) by source position, so the network is stable.
+template <class K, bool VALS, int VT>
+__device__ __forceinline__ void cmp_swap(K (&k)[VT], uint16_t (&g)[VT], int a, int b)
+{
+    const bool swap = VALS ? (k[a] > k[b] || (k[a] == k[b] && g[a] > g[b])) : (k[a] > k[b]);
+    if (swap) {
+        const K tk = k[a]; k[a] = k[b]; k[b] = tk;
+        if constexpr (VALS) {
+            const uint16_t tg = g[a]; g[a] = g[b]; g[b] = tg;
+        }
+    }
+}
+
+// Batcher's odd-even merge sort network on n (a power of two) elements, as
+// a compile-time list of comparator pairs (a < b).
+constexpr int batcher_count(int n)
+{
+    int c = 0;
+    for (int p = 1; p < n; p <<= 1)
+        for (int s = p; s >= 1; s >>= 1)
+            for (int j = s % p; j + s < n; j += 2 * s)
+                for (int i = 0; i < s; ++i)
+                    if (i + j + s < n && (i + j) / (2 * p) == (i + j + s) / (2 * p)) ++c;
+    return c;
+}
+
+template <int VT>
+struct BatcherNet {
+    static constexpr int N = batcher_count(VT);
+    int a[N > 0 ? N : 1];
+    int b[N > 0 ? N : 1];
+    constexpr BatcherNet() : a(), b()
+    {
+        int c = 0;
+        for (int p = 1; p < VT; p <<= 1)
+            for (int s = p; s >= 1; s >>= 1)
+                for (int j = s % p; j + s < VT; j += 2 * s)
+                    for (int i = 0; i < s; ++i)
+                        if (i + j + s < VT && (i + j) / (2 * p) == (i + j + s) / (2 * p)) {
+                            a[c] = i + j;
+                            b[c] = i + j + s;
+                            ++c;
+                        }
+    }
+};
+
+template <class K, bool VALS, int VT>
+__device__ __forceinline__ void register_sort(K (&k)[VT], uint16_t (&g)[VT])
+{
+    constexpr BatcherNet<VT> net;
+#pragma unroll
+    for (int c = 0; c < BatcherNet<VT>::N; ++c) cmp_swap<K, VALS, VT>(k, g, net.a[c], net.b[c]);
+}
+
+// Sorts tile `tile` of in[0..n) into out (out may equal in: a CTA reads its
+// whole tile before writing).
 template <class K, bool VALS, int NT, int VT>
 __device__ __forceinline__ void block_sort_body(const K* in, const uint32_t* vin, K* out,
                                                 uint32_t* vout, int64_t n, Codec<K> c, int64_t tile,
                                                 unsigned char* smem)
 {
+    static_assert((VT & (VT - 1)) == 0, "VT must be a power of two");
     using SM = SortSmem<K, VALS, NT, VT>;
     constexpr int T = SM::T;
     K* sk = reinterpret_cast<K*>(smem);
@@ -34,63 +111,78 @@ __device__ __forceinline__ void block_sort_body(const K* in, const uint32_t* vin
     const int L = (int)(n - base < T ? n - base : T);
     const K pad = ~K(0);  // encoded maximum: sorts after every real key
 
-    // Coalesced load; positions past the end hold the padding key.
+    // 1. Coalesced load; positions past the end hold the padding key.
 #pragma unroll 4
     for (int j = tid; j < T; j += NT) {
-        sk[j] = j < L ? key_enc(in[base + j], c) : pad;
+        sk[padded<K>(j)] = j < L ? key_enc(in[base + j], c) : pad;
         if constexpr (VALS) {
             if (j < L) sv[j] = vin[base + j];
         }
     }
     __syncthreads();
 
+    // 2. Thread-local sort of VT keys.
     K keys[VT];
     uint16_t tags[VT];
 #pragma unroll
     for (int i = 0; i < VT; ++i) {
-        keys[i] = sk[tid * VT + i];
+        keys[i] = sk[padded<K>(tid * VT + i)];
         tags[i] = (uint16_t)(tid * VT + i);
     }
-    // Odd-even transposition sort of VT keys; swapping only strictly greater
-    // neighbours keeps equal keys in order (stable).
-#pragma unroll
-    for (int r = 0; r < VT; ++r) {
-#pragma unroll
-        for (int i = r & 1; i + 1 < VT; i += 2) {
-            if (keys[i] > keys[i + 1]) {
-                K tk = keys[i]; keys[i] = keys[i + 1]; keys[i + 1] = tk;
-                uint16_t tt = tags[i]; tags[i] = tags[i + 1]; tags[i + 1] = tt;
-            }
-        }
-    }
-    // Merge rounds: runs of width w merge pairwise, each thread producing VT
-    // outputs of its pair at diagonal (tid*VT mod 2w).
+    register_sort<K, VALS, VT>(keys, tags);
+
+    // 3. Merge rounds: runs of width w merge pairwise.
     for (int w = VT; w < T; w *= 2) {
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < VT; ++i) {
-            sk[tid * VT + i] = keys[i];
-            stag[tid * VT + i] = tags[i];
+            sk[padded<K>(tid * VT + i)] = keys[i];
+            if constexpr (VALS) stag[padded<uint16_t>(tid * VT + i)] = tags[i];
         }
         __syncthreads();
-        const int gs = (tid * VT) & ~(2 * w - 1);
+        const int gs = (tid * VT) & ~(2 * w - 1);  // start of this thread's run pair
         const int diag = tid * VT - gs;
-        const K* sA = sk + gs;
-        const K* sB = sk + gs + w;
-        const int ai = smem_diagonal_search_enc(sA, w, sB, w, diag);
-        serial_merge_regs<K, VT>(sA, stag + gs, w, sB, stag + gs + w, w, ai, diag - ai, keys, tags);
+        // Diagonal search (Alg. 2) in the pair A = [gs, gs+w), B = [gs+w, gs+2w).
+        int lo = diag - w > 0 ? diag - w : 0;
+        int hi = diag < w ? diag : w;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (sk[padded<K>(gs + mid)] > sk[padded<K>(gs + w + diag - 1 - mid)])
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+        // Serial merge of VT outputs (ties take A).
+        int ai = lo, bi = diag - lo;
+        K ka = sk[padded<K>(gs + (ai < w ? ai : w - 1))];
+        K kb = sk[padded<K>(gs + w + (bi < w ? bi : w - 1))];
+#pragma unroll
+        for (int i = 0; i < VT; ++i) {
+            const bool take_a = (bi >= w) || (ai < w && !(ka > kb));
+            keys[i] = take_a ? ka : kb;
+            if constexpr (VALS)
+                tags[i] = stag[padded<uint16_t>(take_a ? gs + ai : gs + w + bi)];
+            if (take_a) {
+                ++ai;
+                ka = sk[padded<K>(gs + (ai < w ? ai : w - 1))];
+            } else {
+                ++bi;
+                kb = sk[padded<K>(gs + w + (bi < w ? bi : w - 1))];
+            }
+        }
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < VT; ++i) {
-        sk[tid * VT + i] = keys[i];
-        stag[tid * VT + i] = tags[i];
+        sk[padded<K>(tid * VT + i)] = keys[i];
+        if constexpr (VALS) stag[padded<uint16_t>(tid * VT + i)] = tags[i];
     }
     __syncthreads();
+    // 4. Coalesced store.
 #pragma unroll 4
     for (int j = tid; j < L; j += NT) {
-        out[base + j] = key_dec(sk[j], c);
-        if constexpr (VALS) vout[base + j] = sv[stag[j]];
+        out[base + j] = key_dec(sk[padded<K>(j)], c);
+        if constexpr (VALS) vout[base + j] = sv[stag[padded<uint16_t>(j)]];
     }
 }
 
