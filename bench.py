@@ -682,6 +682,22 @@ def run_ours(args):
     }
     if e2e is not None:
         line["e2e"] = e2e
+    # The merge with results kept on chip (Sec. VI, Fig. 5: results written
+    # to a register): the read side alone.
+    readonly = None
+    if not args.no_extras:
+        cs = mp.mp_merge_checksum(A, B, AV, BV)
+        torch.cuda.synchronize(dev)
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        for _ in range(reps):
+            mp.mp_merge_checksum(A, B, AV, BV, out=cs)
+        r1.record(stream)
+        torch.cuda.synchronize(dev)
+        ro_ms = r0.elapsed_time(r1) / reps
+        readonly = {"call": "mp_merge_checksum (partition + merge, outputs folded on chip)",
+                    "ms": ro_ms, "read_gbs": n * 12 / ro_ms / 1e6,
+                    "gkeys_s": n / ro_ms / 1e6}
     if not args.no_extras:
         extras = {}
         wanted = [x for x in args.extras.split(",") if x]
@@ -698,6 +714,8 @@ def run_ours(args):
                 extras[name] = {"error": f"{type(exc).__name__}: {exc}"}
             extras[name]["wall_s"] = time.perf_counter() - t0
             torch.cuda.empty_cache()
+        if readonly is not None:
+            extras["readonly_merge"] = readonly
         line["extras"] = extras
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, reps_o, secs = oracle_rate(a, av, b, bv)

@@ -189,6 +189,25 @@ MP_API mp_status mp_merge_pairs_host(mp_dtype dtype,
                                      void* out_keys, uint32_t* out_vals, mp_stream_t stream);
 
 /*
+ * mp_merge_checksum -- the merge with its results kept on chip: the
+ * experiment in Sec. VI (Fig. 5) that writes merge results to a register
+ * instead of memory, to separate the read side from the write side.
+ *   Merges A and B (values too when a_vals/b_vals are set) exactly as
+ *   mp_merge_pairs would, but stores nothing: every output j (key bits k_j
+ *   zero-extended to 64 bits, value v_j or 0) is folded into
+ *   *checksum = sum over j of f(k_j, v_j, j) mod 2^64 with
+ *     h = k_j * 0x9E3779B97F4A7C15;  h ^= v_j * 0xBF58476D1CE4E5B9 (values only);
+ *     h ^= (j + 1) * 0x94D049BB133111EB;  f = h ^ (h >> 29),
+ *   an order-sensitive digest of the merged sequence.  checksum: device
+ *   pointer to one 8-byte-aligned uint64, zeroed by the call then
+ *   accumulated.  Global traffic: the read of A and B only.
+ */
+MP_API mp_status mp_merge_checksum(mp_dtype dtype,
+                                   const void* a_keys, const uint32_t* a_vals, int64_t na,
+                                   const void* b_keys, const uint32_t* b_vals, int64_t nb,
+                                   uint64_t* checksum, mp_stream_t stream);
+
+/*
  * mp_sort_workspace_bytes -- device workspace that mp_sort needs for n keys
  * (with_values != 0: plus uint32 values).  0 for n <= 1.
  */

@@ -115,6 +115,7 @@ _SIGNATURES = {
     "mp_clock_seconds": ([], ctypes.c_double),
     "mp_kernel_error": ([ctypes.POINTER(ctypes.c_uint), _I32], _I32),
     "mp_merge_noalloc": ([_I32, _P, _P, _I64, _P, _P, _I64, _P, _P, _P], _I32),
+    "mp_merge_checksum": ([_I32, _P, _P, _I64, _P, _P, _I64, _P, _P], _I32),
     "mp_autotune_merge": ([_I32, _P, _P, _I64, _P, _P, _I64, _P, _P, _I32, ctypes.POINTER(mp_plan), _P], _I32),
     "mp_autotune_batched": ([_I32, _P, _P, _P, _P, _I64, _I64, _I64, _P, _P, _P, _P, _I32,
                              ctypes.POINTER(mp_plan), _P], _I32),
@@ -261,6 +262,19 @@ def mp_plan_supported(plan) -> bool:
     p = plan if isinstance(plan, mp_plan) else mp_plan(int(plan[0]), int(plan[1]),
                                                        int(plan[2]) if len(plan) > 2 else 0, 0)
     return bool(lib().mp_plan_supported(ctypes.byref(p)))
+
+
+def mp_merge_checksum(a_keys, b_keys, a_vals=None, b_vals=None, out=None, stream=None):
+    """Merge without storing (results folded into an order-sensitive uint64
+    digest on the device); returns the 1-element int64 device tensor."""
+    if out is None:
+        out = torch.empty(1, dtype=torch.int64, device=a_keys.device)
+    pairs = a_vals is not None
+    _check(lib().mp_merge_checksum(_dtype_code(a_keys), _dev(a_keys, "a_keys"),
+                                   _vals(a_vals, "a_vals") if pairs else None, a_keys.numel(),
+                                   _dev(b_keys, "b_keys"), _vals(b_vals, "b_vals") if pairs else None,
+                                   b_keys.numel(), _dev(out, "checksum"), _stream(stream)))
+    return out
 
 
 def mp_merge_tile_items(dtype, with_values: bool, total: int, plan=None) -> int:

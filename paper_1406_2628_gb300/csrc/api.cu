@@ -347,6 +347,48 @@ mp_status mp_merge_pairs_host(mp_dtype dtype, const void* a_keys, const uint32_t
     return MP_OK;
 }
 
+mp_status mp_merge_checksum(mp_dtype dtype, const void* a_keys, const uint32_t* a_vals, int64_t na,
+                            const void* b_keys, const uint32_t* b_vals, int64_t nb, uint64_t* checksum,
+                            mp_stream_t stream)
+{
+    KeyKind k;
+    if (!key_kind(dtype, &k)) return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_merge_checksum: unknown dtype");
+    if (!checksum || ((uintptr_t)checksum & 7)) return fail(MP_ERR_INVALID_ARG, "mp_merge_checksum: checksum must be an aligned device pointer");
+    const bool vals = a_vals || b_vals;
+    if (na < 0 || nb < 0) return fail(MP_ERR_INVALID_ARG, "mp_merge_checksum: negative size");
+    if ((na > 0 && !a_keys) || (nb > 0 && !b_keys))
+        return fail(MP_ERR_INVALID_ARG, "mp_merge_checksum: NULL key pointer");
+    if (!aligned(a_keys, k.bytes) || !aligned(b_keys, k.bytes))
+        return fail(MP_ERR_INVALID_ARG, "mp_merge_checksum: key pointer not aligned to the key size");
+    if (vals && ((na > 0 && !a_vals) || (nb > 0 && !b_vals)))
+        return fail(MP_ERR_INVALID_ARG, "mp_merge_checksum: NULL value array for a non-empty side");
+    if (vals && (!aligned(a_vals, 4) || !aligned(b_vals, 4)))
+        return fail(MP_ERR_INVALID_ARG, "mp_merge_checksum: value pointer not 4-byte aligned");
+    mp_status st = MP_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(checksum, 0, 8, s);
+    if (e != cudaSuccess) return cuda_fail(e, "mp_merge_checksum");
+    if (na + nb == 0) return MP_OK;
+    MergeProblem p = {};
+    p.kind = k;
+    p.vals = vals;
+    p.a = a_keys;
+    p.b = b_keys;
+    p.av = a_vals;
+    p.bv = b_vals;
+    p.na = na;
+    p.nb = nb;
+    const int64_t T = checksum_tile(k.bytes, vals);
+    const int64_t bounds = ceil_div(na + nb, T) + 1;
+    int64_t* splits = nullptr;
+    st = scratch_alloc((void**)&splits, (size_t)bounds * 8, s);
+    if (st != MP_OK) return st;
+    e = launch_partition(p, T, splits, s);
+    if (e == cudaSuccess) e = launch_merge_checksum(p, splits, (unsigned long long*)checksum, s);
+    scratch_free(splits, s);
+    return e == cudaSuccess ? MP_OK : cuda_fail(e, "mp_merge_checksum");
+}
+
 mp_status mp_merge_path_partition(mp_dtype dtype, const void* a, int64_t na, const void* b,
                                   int64_t nb, int64_t spacing, int64_t* a_split, mp_stream_t stream)
 {

@@ -129,6 +129,13 @@ __device__ __forceinline__ void batched_thread_merge(const BatchArgs<K>& p, cons
     const int diag = tid * VT < L ? tid * VT : L;
     if (diag >= L) return;
     uint32_t packed[VT / 2];
+    if (bt.s0 == bt.s1) {
+        // The whole tile lies in one segment: a plain Merge Path tile.
+        const int ai = smem_diagonal_search(v.sA, la, v.sB, lb, diag, c);
+        serial_merge_indices<K, VT>(v.sA, la, v.sB, lb, ai, diag - ai, c, packed);
+        put_indices<VT>(v.sidx, packed);
+        return;
+    }
     const int64_t dg = bt.d0 + diag;
     int64_t s = segment_of(p.a_off, p.b_off, bt.s0, bt.s1, dg);
     const int64_t aS = __ldg(p.a_off + s), aE = __ldg(p.a_off + s + 1);

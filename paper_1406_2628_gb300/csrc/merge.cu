@@ -56,6 +56,15 @@ __global__ void __launch_bounds__(NT) merge_tile_bulk_kernel(TileArgs<K> p, unsi
     merge_tile_bulk_body<K, VALS, NT, VT, CK>(p, blockIdx.x, p.a_split, smem, err);
 }
 
+template <class K, bool VALS, int NT, int VT, int CK>
+__global__ void __launch_bounds__(NT) merge_tile_checksum_kernel(TileArgs<K> p, unsigned int* err,
+                                                                 unsigned long long* sum)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    merge_tile_checksum_body<K, VALS, NT, VT, CK>(p, blockIdx.x, p.a_split, smem, err, sum);
+}
+
 // Device address of the kernel error word on the current device.
 unsigned int* kernel_error_word()
 {
@@ -272,3 +281,49 @@ extern "C" mp_status mp_kernel_error(unsigned int* code, int reset)
     if (code) *code = v;
     return MP_OK;
 }
+
+namespace mp {
+
+template <class K, bool VALS, int CK>
+static cudaError_t launch_checksum_t(const MergeProblem& p, const int64_t* a_split,
+                                     unsigned long long* sum, cudaStream_t stream)
+{
+    constexpr int NT = 256, VT = VALS ? 8 : 16;
+    using SM = BulkSmem<K, VALS, NT, VT>;
+    auto kern = merge_tile_checksum_kernel<K, VALS, NT, VT, CK>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    unsigned int* err = kernel_error_word();
+    if (!err) return cudaErrorInvalidSymbol;
+    const int64_t tiles = ceil_div(p.total(), (int64_t)NT * VT);
+    kern<<<(unsigned)tiles, NT, SM::bytes, stream>>>(make_args<K>(p, a_split), err, sum);
+    return cudaGetLastError();
+}
+
+int64_t checksum_tile(int key_bytes, bool vals)
+{
+    (void)key_bytes;
+    return 256 * (vals ? 8 : 16);
+}
+
+cudaError_t launch_merge_checksum(const MergeProblem& p, const int64_t* a_split, unsigned long long* sum,
+                                  cudaStream_t stream)
+{
+    const bool id = p.kind.flip == 0 && p.kind.fmask == 0;
+    if (p.kind.bytes == 4) {
+        if (p.vals) return id ? launch_checksum_t<uint32_t, true, CODEC_IDENTITY>(p, a_split, sum, stream)
+                              : launch_checksum_t<uint32_t, true, CODEC_RUNTIME>(p, a_split, sum, stream);
+        return id ? launch_checksum_t<uint32_t, false, CODEC_IDENTITY>(p, a_split, sum, stream)
+                  : launch_checksum_t<uint32_t, false, CODEC_RUNTIME>(p, a_split, sum, stream);
+    }
+    if (p.vals) return id ? launch_checksum_t<uint64_t, true, CODEC_IDENTITY>(p, a_split, sum, stream)
+                          : launch_checksum_t<uint64_t, true, CODEC_RUNTIME>(p, a_split, sum, stream);
+    return id ? launch_checksum_t<uint64_t, false, CODEC_IDENTITY>(p, a_split, sum, stream)
+              : launch_checksum_t<uint64_t, false, CODEC_RUNTIME>(p, a_split, sum, stream);
+}
+
+}  // namespace mp

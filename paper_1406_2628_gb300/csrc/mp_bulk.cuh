@@ -273,4 +273,55 @@ __device__ __forceinline__ void merge_tile_bulk_body(const TileArgs<K>& p, int64
     store_tile<K, VALS, NT, VT>(v, p.out + t.d0, VALS ? p.outv + t.d0 : nullptr);
 }
 
+// Order-sensitive fold of one merged output (key bits, value, position)
+// into 64 bits; the checksum of a merge is the sum of these over all
+// outputs (mod 2^64).
+__device__ __forceinline__ uint64_t output_fold(uint64_t key, uint32_t val, bool vals, uint64_t pos)
+{
+    uint64_t h = key * 0x9E3779B97F4A7C15ull;
+    if (vals) h ^= (uint64_t)val * 0xBF58476D1CE4E5B9ull;
+    h ^= (pos + 1) * 0x94D049BB133111EBull;
+    return h ^ (h >> 29);
+}
+
+// The merge with its results kept on chip: the tile is staged and merged as
+// in merge_tile_bulk_body, but instead of being stored each output is folded
+// into a per-thread sum, reduced over the warp and added to *sum.  Global
+// traffic is the read of A and B only (Sec. VI measures this variant to
+// separate reading from writing).
+template <class K, bool VALS, int NT, int VT, int CK>
+__device__ __forceinline__ void merge_tile_checksum_body(const TileArgs<K>& p, int64_t tile,
+                                                         const int64_t* a_split, unsigned char* smem,
+                                                         unsigned int* err,
+                                                         unsigned long long* sum)
+{
+    constexpr int T = NT * VT;
+    const int tid = threadIdx.x;
+    const BulkLayout<K, VALS, NT, VT> lay(smem);
+    const TilePlace<K> t = tile_place(p, tile, T, a_split);
+    const auto v = stage_view<K, VALS, NT, VT>(t, lay.sk, lay.sv, lay.sidx);
+    bulk_init(lay.bar);
+    __syncthreads();
+    if (!bulk_stage<K, VALS, NT, VT>(t, v, lay.bar, 0, err)) return;
+    const int L = t.la + t.lb;
+    const int diag = tid * VT < L ? tid * VT : L;
+    const int ai = smem_diagonal_search_ck<CK>(v.sA, t.la, v.sB, t.lb, diag, p.codec);
+    uint32_t packed[VT / 2];
+    serial_merge_indices_ck<K, VT, CK>(v.sA, t.la, v.sB, t.lb, ai, diag - ai, p.codec, packed);
+    uint64_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < VT; ++i) {
+        if (diag + i < L) {
+            const int src = (packed[i / 2] >> (16 * (i & 1))) & 0xFFFF;
+            const K key = src < t.la ? v.sA[src] : v.sB[src - t.la];
+            uint32_t val = 0;
+            if constexpr (VALS) val = src < t.la ? v.vA[src] : v.vB[src - t.la];
+            acc += output_fold((uint64_t)key, val, VALS, (uint64_t)(t.d0 + diag + i));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if ((tid & 31) == 0 && acc) atomicAdd(sum, (unsigned long long)acc);
+}
+
 }  // namespace mp

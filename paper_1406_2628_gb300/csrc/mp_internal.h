@@ -132,6 +132,11 @@ mp_status check_merge_args_ext(const KeyKind& k, const void* a, const uint32_t* 
                                const void* b, const uint32_t* bv, int64_t nb, const void* out,
                                const uint32_t* outv, bool vals, const char* fn);
 
+// Read-only merge (results folded into a checksum, merge.cu).
+int64_t checksum_tile(int key_bytes, bool vals);
+cudaError_t launch_merge_checksum(const MergeProblem& p, const int64_t* a_split,
+                                  unsigned long long* sum, cudaStream_t stream);
+
 // Device address of the word kernels set when a bounded wait runs out.
 unsigned int* kernel_error_word();
 
