@@ -10,7 +10,8 @@
  *
  * Conventions shared by every entry point
  * ----------------------------------------
- *  - Order: ascending.  Keys compare in their natural order; MP_F32 keys
+ *  - Order: ascending, or descending with MP_DESCENDING.  Keys compare in
+ *    their natural order; MP_F32 keys
  *    compare in IEEE-754 numeric order with -0.0 before +0.0.  NaN keys are
  *    outside the contract (mp_check_sorted reports them).  Merges are stable:
  *    on equal keys A's element comes first (Sec. II.A: the path moves right,
@@ -75,6 +76,13 @@ typedef enum mp_dtype {
     MP_U64 = 3, /* uint64_t */
     MP_I64 = 4  /* int64_t  */
 } mp_dtype;
+
+/* Order flag, OR'ed into the dtype argument of any entry point: keys are in
+ * DESCENDING order (inputs sorted descending, results descending).  The
+ * paper assumes ascending order without loss of generality (Sec. II.A); the
+ * descending merge is the same method on complemented keys, and stays
+ * stable (on equal keys A's element still comes first). */
+#define MP_DESCENDING 0x100
 
 /* Tile shape of the merge kernels.  block_threads (NT) threads per CTA, each
  * producing items_per_thread (VT) outputs, so one CTA produces a tile of

@@ -35,6 +35,7 @@ MP_ERR_NOT_READY = 10
 
 # mp_dtype
 MP_I32, MP_U32, MP_F32, MP_U64, MP_I64 = 0, 1, 2, 3, 4
+MP_DESCENDING = 0x100  # OR'ed into a dtype: descending key order
 
 # request queue enums
 MP_OP_MERGE, MP_OP_SORT = 0, 1
@@ -166,9 +167,9 @@ def _check(status: int):
         raise MPError(status, detail)
 
 
-def _dtype_code(t: torch.Tensor) -> int:
+def _dtype_code(t: torch.Tensor, descending: bool = False) -> int:
     try:
-        return _TORCH_DTYPE[t.dtype]
+        return _TORCH_DTYPE[t.dtype] | (MP_DESCENDING if descending else 0)
     except KeyError:
         raise TypeError(f"unsupported key dtype {t.dtype}") from None
 
@@ -213,18 +214,18 @@ def mp_last_error() -> str:
 
 
 def mp_merge_keys(a: torch.Tensor, b: torch.Tensor, out: torch.Tensor | None = None,
-                  stream=None) -> torch.Tensor:
+                  stream=None, descending: bool = False) -> torch.Tensor:
     """Stable merge of sorted 1-D tensors a and b (ties: a first)."""
     if a.dtype != b.dtype:
         raise TypeError("a and b must have the same dtype")
     if out is None:
         out = torch.empty(a.numel() + b.numel(), dtype=a.dtype, device=a.device)
-    _check(lib().mp_merge_keys(_dtype_code(a), _dev(a, "a"), a.numel(), _dev(b, "b"), b.numel(),
+    _check(lib().mp_merge_keys(_dtype_code(a, descending), _dev(a, "a"), a.numel(), _dev(b, "b"), b.numel(),
                                _dev(out, "out"), _stream(stream)))
     return out
 
 
-def mp_merge_pairs(a_keys, a_vals, b_keys, b_vals, out_keys=None, out_vals=None, stream=None):
+def mp_merge_pairs(a_keys, a_vals, b_keys, b_vals, out_keys=None, out_vals=None, stream=None, descending: bool = False):
     """Stable merge moving a uint32 payload with each key."""
     if a_keys.dtype != b_keys.dtype:
         raise TypeError("key dtypes differ")
@@ -233,7 +234,7 @@ def mp_merge_pairs(a_keys, a_vals, b_keys, b_vals, out_keys=None, out_vals=None,
         out_keys = torch.empty(n, dtype=a_keys.dtype, device=a_keys.device)
     if out_vals is None:
         out_vals = torch.empty(n, dtype=a_vals.dtype, device=a_keys.device)
-    _check(lib().mp_merge_pairs(_dtype_code(a_keys), _dev(a_keys, "a_keys"), _vals(a_vals, "a_vals"),
+    _check(lib().mp_merge_pairs(_dtype_code(a_keys, descending), _dev(a_keys, "a_keys"), _vals(a_vals, "a_vals"),
                                 a_keys.numel(), _dev(b_keys, "b_keys"), _vals(b_vals, "b_vals"),
                                 b_keys.numel(), _dev(out_keys, "out_keys"), _vals(out_vals, "out_vals"),
                                 _stream(stream)))
@@ -241,7 +242,7 @@ def mp_merge_pairs(a_keys, a_vals, b_keys, b_vals, out_keys=None, out_vals=None,
 
 
 def mp_merge_plan(a_keys, b_keys, a_vals=None, b_vals=None, out_keys=None, out_vals=None,
-                  plan=None, stream=None):
+                  plan=None, stream=None, descending: bool = False):
     """Merge with an explicit tile plan (block_threads, items_per_thread[, staging])."""
     n = a_keys.numel() + b_keys.numel()
     if out_keys is None:
@@ -249,7 +250,7 @@ def mp_merge_plan(a_keys, b_keys, a_vals=None, b_vals=None, out_keys=None, out_v
     pairs = a_vals is not None
     if pairs and out_vals is None:
         out_vals = torch.empty(n, dtype=a_vals.dtype, device=a_keys.device)
-    _check(lib().mp_merge_plan(_dtype_code(a_keys), _dev(a_keys, "a_keys"),
+    _check(lib().mp_merge_plan(_dtype_code(a_keys, descending), _dev(a_keys, "a_keys"),
                                _vals(a_vals, "a_vals") if pairs else None, a_keys.numel(),
                                _dev(b_keys, "b_keys"), _vals(b_vals, "b_vals") if pairs else None,
                                b_keys.numel(), _dev(out_keys, "out_keys"),
@@ -264,13 +265,13 @@ def mp_plan_supported(plan) -> bool:
     return bool(lib().mp_plan_supported(ctypes.byref(p)))
 
 
-def mp_merge_checksum(a_keys, b_keys, a_vals=None, b_vals=None, out=None, stream=None):
+def mp_merge_checksum(a_keys, b_keys, a_vals=None, b_vals=None, out=None, stream=None, descending: bool = False):
     """Merge without storing (results folded into an order-sensitive uint64
     digest on the device); returns the 1-element int64 device tensor."""
     if out is None:
         out = torch.empty(1, dtype=torch.int64, device=a_keys.device)
     pairs = a_vals is not None
-    _check(lib().mp_merge_checksum(_dtype_code(a_keys), _dev(a_keys, "a_keys"),
+    _check(lib().mp_merge_checksum(_dtype_code(a_keys, descending), _dev(a_keys, "a_keys"),
                                    _vals(a_vals, "a_vals") if pairs else None, a_keys.numel(),
                                    _dev(b_keys, "b_keys"), _vals(b_vals, "b_vals") if pairs else None,
                                    b_keys.numel(), _dev(out, "checksum"), _stream(stream)))
@@ -321,13 +322,13 @@ def mp_merge_pairs_host(a_keys, a_vals, b_keys, b_vals, out_keys, out_vals, stre
     return (out_keys, out_vals) if pairs else out_keys
 
 
-def mp_merge_path_partition(a, b, spacing: int, out=None, stream=None):
+def mp_merge_path_partition(a, b, spacing: int, out=None, stream=None, descending: bool = False):
     """Split points (Alg. 2) at diagonals min(t*spacing, |a|+|b|)."""
     n = a.numel() + b.numel()
     nb = (n + spacing - 1) // spacing + 1
     if out is None:
         out = torch.empty(nb, dtype=torch.int64, device=a.device)
-    _check(lib().mp_merge_path_partition(_dtype_code(a), _dev(a, "a"), a.numel(), _dev(b, "b"),
+    _check(lib().mp_merge_path_partition(_dtype_code(a, descending), _dev(a, "a"), a.numel(), _dev(b, "b"),
                                          b.numel(), int(spacing), _dev(out, "a_split"),
                                          _stream(stream)))
     return out
@@ -338,20 +339,20 @@ def mp_sort_workspace_bytes(dtype, n: int, with_values: bool) -> int:
     return int(lib().mp_sort_workspace_bytes(code, int(n), 1 if with_values else 0))
 
 
-def mp_sort(keys, vals=None, workspace=None, stream=None):
+def mp_sort(keys, vals=None, workspace=None, stream=None, descending: bool = False):
     """Stable in-place merge sort of keys (and vals)."""
     n = keys.numel()
     need = mp_sort_workspace_bytes(keys.dtype, n, vals is not None)
     if workspace is None:
         workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=keys.device)
-    _check(lib().mp_sort(_dtype_code(keys), _dev(keys, "keys"),
+    _check(lib().mp_sort(_dtype_code(keys, descending), _dev(keys, "keys"),
                          _vals(vals, "vals") if vals is not None else None, n,
                          _dev(workspace, "workspace"), workspace.numel(), _stream(stream)))
     return (keys, vals) if vals is not None else keys
 
 
 def mp_merge_batched(a, a_off, b, b_off, out=None, a_vals=None, b_vals=None, out_vals=None,
-                     na_total=None, nb_total=None, plan=None, stream=None):
+                     na_total=None, nb_total=None, plan=None, stream=None, descending: bool = False):
     """nseg independent stable merges (offsets: int64 device tensors, nseg+1)."""
     nseg = a_off.numel() - 1
     if na_total is None:
@@ -364,7 +365,7 @@ def mp_merge_batched(a, a_off, b, b_off, out=None, a_vals=None, b_vals=None, out
     pairs = a_vals is not None
     if pairs and out_vals is None:
         out_vals = torch.empty(n, dtype=a_vals.dtype, device=a.device)
-    _check(lib().mp_merge_batched(_dtype_code(a), _dev(a, "a"), _dev(a_off, "a_off"), _dev(b, "b"),
+    _check(lib().mp_merge_batched(_dtype_code(a, descending), _dev(a, "a"), _dev(a_off, "a_off"), _dev(b, "b"),
                                   _dev(b_off, "b_off"), nseg, int(na_total), int(nb_total),
                                   _dev(out, "out"), _vals(a_vals, "a_vals") if pairs else None,
                                   _vals(b_vals, "b_vals") if pairs else None,
@@ -395,9 +396,9 @@ def mp_merge_grouped(problems, with_values: bool = False, stream=None):
     _check(lib().mp_merge_grouped(arr, n, 1 if with_values else 0, _stream(stream)))
 
 
-def mp_check_sorted(keys, stream=None) -> int:
+def mp_check_sorted(keys, stream=None, descending: bool = False) -> int:
     """Synchronous: MP_OK, MP_ERR_NOT_SORTED or MP_ERR_NAN."""
-    return int(lib().mp_check_sorted(_dtype_code(keys), _dev(keys, "keys"), keys.numel(),
+    return int(lib().mp_check_sorted(_dtype_code(keys, descending), _dev(keys, "keys"), keys.numel(),
                                      _stream(stream)))
 
 

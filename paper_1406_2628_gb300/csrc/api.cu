@@ -27,14 +27,18 @@ mp_status cuda_fail(cudaError_t err, const char* where)
 
 bool key_kind(mp_dtype dtype, KeyKind* k)
 {
-    switch (dtype) {
-    case MP_I32: *k = {4, 0x80000000ull, 0}; return true;
-    case MP_U32: *k = {4, 0, 0}; return true;
-    case MP_F32: *k = {4, 0x80000000ull, 0xFFFFFFFFull}; return true;
-    case MP_U64: *k = {8, 0, 0}; return true;
-    case MP_I64: *k = {8, 0x8000000000000000ull, 0}; return true;
+    const int d = (int)dtype;
+    if (d & ~(0xFF | MP_DESCENDING)) return false;
+    switch (d & 0xFF) {
+    case MP_I32: *k = {4, 0x80000000ull, 0, 0}; break;
+    case MP_U32: *k = {4, 0, 0, 0}; break;
+    case MP_F32: *k = {4, 0x80000000ull, 0xFFFFFFFFull, 0}; break;
+    case MP_U64: *k = {8, 0, 0, 0}; break;
+    case MP_I64: *k = {8, 0x8000000000000000ull, 0, 0}; break;
+    default: return false;
     }
-    return false;
+    if (d & MP_DESCENDING) k->inv = k->bytes == 8 ? ~0ull : 0xFFFFFFFFull;
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -381,10 +385,13 @@ mp_status mp_merge_checksum(mp_dtype dtype, const void* a_keys, const uint32_t* 
     const int64_t T = checksum_tile(k.bytes, vals);
     const int64_t bounds = ceil_div(na + nb, T) + 1;
     int64_t* splits = nullptr;
-    st = scratch_alloc((void**)&splits, (size_t)bounds * 8, s);
+    // Split points, then one partial digest per tile.
+    st = scratch_alloc((void**)&splits, (size_t)bounds * 16, s);
     if (st != MP_OK) return st;
     e = launch_partition(p, T, splits, s);
-    if (e == cudaSuccess) e = launch_merge_checksum(p, splits, (unsigned long long*)checksum, s);
+    if (e == cudaSuccess)
+        e = launch_merge_checksum(p, splits, (unsigned long long*)(splits + bounds),
+                                  (unsigned long long*)checksum, s);
     scratch_free(splits, s);
     return e == cudaSuccess ? MP_OK : cuda_fail(e, "mp_merge_checksum");
 }
@@ -458,11 +465,12 @@ mp_status mp_check_sorted(mp_dtype dtype, const void* keys, int64_t n, mp_stream
     if (e == cudaSuccess) {
         if (k.bytes == 4)
             check_sorted_kernel<uint32_t><<<(unsigned)blocks, threads, 0, s>>>(
-                (const uint32_t*)keys, n, Codec<uint32_t>{(uint32_t)k.flip, (uint32_t)k.fmask},
-                dtype == MP_F32, flags);
+                (const uint32_t*)keys, n,
+                Codec<uint32_t>{(uint32_t)k.flip, (uint32_t)k.fmask, (uint32_t)k.inv},
+                ((int)dtype & 0xFF) == MP_F32, flags);
         else
             check_sorted_kernel<uint64_t><<<(unsigned)blocks, threads, 0, s>>>(
-                (const uint64_t*)keys, n, Codec<uint64_t>{k.flip, k.fmask}, false, flags);
+                (const uint64_t*)keys, n, Codec<uint64_t>{k.flip, k.fmask, k.inv}, false, flags);
         e = cudaGetLastError();
     }
     unsigned host_flags = 0;

@@ -270,6 +270,7 @@ static BatchArgs<K> make_batch_args(const BatchedProblem& q, int64_t tile, const
     p.seg_split = seg_split;
     p.codec.flip = (K)q.kind.flip;
     p.codec.fmask = (K)q.kind.fmask;
+    p.codec.inv = (K)q.kind.inv;
     return p;
 }
 

@@ -52,6 +52,7 @@ __device__ __forceinline__ TileArgs<K> tile_args_of(const GroupMergeDesc& g)
     p.a_split = nullptr;
     p.codec.flip = (K)g.flip;
     p.codec.fmask = (K)g.fmask;
+    p.codec.inv = (K)g.inv;
     return p;
 }
 
@@ -99,6 +100,7 @@ __global__ void __launch_bounds__(NT) grouped_block_sort_kernel(const GroupSortD
     Codec<K> c;
     c.flip = (K)d.flip;
     c.fmask = (K)d.fmask;
+    c.inv = (K)d.inv;
     block_sort_body<K, VALS, NT, VT>(static_cast<const K*>(d.in), d.vin, static_cast<K*>(d.out),
                                      d.vout, d.n, c, tile - __ldg(tile_first + p), smem);
 }
@@ -224,6 +226,7 @@ extern "C" mp_status mp_merge_grouped(const mp_merge_desc* descs, int64_t nprob,
         g.run = 0;
         g.flip = k.flip;
         g.fmask = k.fmask;
+        g.inv = k.inv;
         first[i] = tiles;
         first[nprob + i] = tiles + i;
         tiles += ceil_div(d.na + d.nb, T);

@@ -56,13 +56,31 @@ __global__ void __launch_bounds__(NT) merge_tile_bulk_kernel(TileArgs<K> p, unsi
     merge_tile_bulk_body<K, VALS, NT, VT, CK>(p, blockIdx.x, p.a_split, smem, err);
 }
 
+// Sum of n partial digests into *sum (one CTA).
+__global__ void __launch_bounds__(1024) sum_partials_kernel(const unsigned long long* partial, int64_t n,
+                                                            unsigned long long* sum)
+{
+    __shared__ unsigned long long ws[32];
+    unsigned long long acc = 0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += partial[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        *sum = t;
+    }
+}
+
 template <class K, bool VALS, int NT, int VT, int CK>
 __global__ void __launch_bounds__(NT) merge_tile_checksum_kernel(TileArgs<K> p, unsigned int* err,
-                                                                 unsigned long long* sum)
+                                                                 unsigned long long* partial)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    merge_tile_checksum_body<K, VALS, NT, VT, CK>(p, blockIdx.x, p.a_split, smem, err, sum);
+    merge_tile_checksum_body<K, VALS, NT, VT, CK>(p, blockIdx.x, p.a_split, smem, err, partial);
 }
 
 // Device address of the kernel error word on the current device.
@@ -99,6 +117,7 @@ static TileArgs<K> make_args(const MergeProblem& p, const int64_t* a_split)
     t.a_split = a_split;
     t.codec.flip = (K)p.kind.flip;
     t.codec.fmask = (K)p.kind.fmask;
+    t.codec.inv = (K)p.kind.inv;
     return t;
 }
 
@@ -147,7 +166,7 @@ static cudaError_t launch_tiles_ck(const MergeProblem& p, const int64_t* a_split
 template <class K, bool VALS, int NT, int VT>
 static cudaError_t launch_tiles_t(const MergeProblem& p, const int64_t* a_split, cudaStream_t stream)
 {
-    if (p.kind.flip == 0 && p.kind.fmask == 0)
+    if (p.kind.identity())
         return launch_tiles_ck<K, VALS, NT, VT, CODEC_IDENTITY>(p, a_split, stream);
     return launch_tiles_ck<K, VALS, NT, VT, CODEC_RUNTIME>(p, a_split, stream);
 }
@@ -182,7 +201,7 @@ static cudaError_t launch_bulk_ck(const MergeProblem& p, const int64_t* a_split,
 template <class K, bool VALS, int NT, int VT>
 static cudaError_t launch_bulk_t(const MergeProblem& p, const int64_t* a_split, cudaStream_t stream)
 {
-    if (p.kind.flip == 0 && p.kind.fmask == 0)
+    if (p.kind.identity())
         return launch_bulk_ck<K, VALS, NT, VT, CODEC_IDENTITY>(p, a_split, stream);
     return launch_bulk_ck<K, VALS, NT, VT, CODEC_RUNTIME>(p, a_split, stream);
 }
@@ -286,7 +305,8 @@ namespace mp {
 
 template <class K, bool VALS, int CK>
 static cudaError_t launch_checksum_t(const MergeProblem& p, const int64_t* a_split,
-                                     unsigned long long* sum, cudaStream_t stream)
+                                     unsigned long long* partial, unsigned long long* sum,
+                                     cudaStream_t stream)
 {
     constexpr int NT = 256, VT = VALS ? 8 : 16;
     using SM = BulkSmem<K, VALS, NT, VT>;
@@ -300,7 +320,10 @@ static cudaError_t launch_checksum_t(const MergeProblem& p, const int64_t* a_spl
     unsigned int* err = kernel_error_word();
     if (!err) return cudaErrorInvalidSymbol;
     const int64_t tiles = ceil_div(p.total(), (int64_t)NT * VT);
-    kern<<<(unsigned)tiles, NT, SM::bytes, stream>>>(make_args<K>(p, a_split), err, sum);
+    kern<<<(unsigned)tiles, NT, SM::bytes, stream>>>(make_args<K>(p, a_split), err, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sum_partials_kernel<<<1, 1024, 0, stream>>>(partial, tiles, sum);
     return cudaGetLastError();
 }
 
@@ -310,20 +333,21 @@ int64_t checksum_tile(int key_bytes, bool vals)
     return 256 * (vals ? 8 : 16);
 }
 
-cudaError_t launch_merge_checksum(const MergeProblem& p, const int64_t* a_split, unsigned long long* sum,
+cudaError_t launch_merge_checksum(const MergeProblem& p, const int64_t* a_split,
+                                  unsigned long long* partial, unsigned long long* sum,
                                   cudaStream_t stream)
 {
-    const bool id = p.kind.flip == 0 && p.kind.fmask == 0;
+    const bool id = p.kind.identity();
     if (p.kind.bytes == 4) {
-        if (p.vals) return id ? launch_checksum_t<uint32_t, true, CODEC_IDENTITY>(p, a_split, sum, stream)
-                              : launch_checksum_t<uint32_t, true, CODEC_RUNTIME>(p, a_split, sum, stream);
-        return id ? launch_checksum_t<uint32_t, false, CODEC_IDENTITY>(p, a_split, sum, stream)
-                  : launch_checksum_t<uint32_t, false, CODEC_RUNTIME>(p, a_split, sum, stream);
+        if (p.vals) return id ? launch_checksum_t<uint32_t, true, CODEC_IDENTITY>(p, a_split, partial, sum, stream)
+                              : launch_checksum_t<uint32_t, true, CODEC_RUNTIME>(p, a_split, partial, sum, stream);
+        return id ? launch_checksum_t<uint32_t, false, CODEC_IDENTITY>(p, a_split, partial, sum, stream)
+                  : launch_checksum_t<uint32_t, false, CODEC_RUNTIME>(p, a_split, partial, sum, stream);
     }
-    if (p.vals) return id ? launch_checksum_t<uint64_t, true, CODEC_IDENTITY>(p, a_split, sum, stream)
-                          : launch_checksum_t<uint64_t, true, CODEC_RUNTIME>(p, a_split, sum, stream);
-    return id ? launch_checksum_t<uint64_t, false, CODEC_IDENTITY>(p, a_split, sum, stream)
-              : launch_checksum_t<uint64_t, false, CODEC_RUNTIME>(p, a_split, sum, stream);
+    if (p.vals) return id ? launch_checksum_t<uint64_t, true, CODEC_IDENTITY>(p, a_split, partial, sum, stream)
+                          : launch_checksum_t<uint64_t, true, CODEC_RUNTIME>(p, a_split, partial, sum, stream);
+    return id ? launch_checksum_t<uint64_t, false, CODEC_IDENTITY>(p, a_split, partial, sum, stream)
+              : launch_checksum_t<uint64_t, false, CODEC_RUNTIME>(p, a_split, partial, sum, stream);
 }
 
 }  // namespace mp

@@ -286,14 +286,14 @@ __device__ __forceinline__ uint64_t output_fold(uint64_t key, uint32_t val, bool
 
 // The merge with its results kept on chip: the tile is staged and merged as
 // in merge_tile_bulk_body, but instead of being stored each output is folded
-// into a per-thread sum, reduced over the warp and added to *sum.  Global
-// traffic is the read of A and B only (Sec. VI measures this variant to
-// separate reading from writing).
+// into a per-thread sum, reduced over the CTA and written to partial[tile]
+// (a second kernel adds the partials).  Global traffic is the read of A and
+// B only (Sec. VI measures this variant to separate reading from writing).
 template <class K, bool VALS, int NT, int VT, int CK>
 __device__ __forceinline__ void merge_tile_checksum_body(const TileArgs<K>& p, int64_t tile,
                                                          const int64_t* a_split, unsigned char* smem,
                                                          unsigned int* err,
-                                                         unsigned long long* sum)
+                                                         unsigned long long* partial)
 {
     constexpr int T = NT * VT;
     const int tid = threadIdx.x;
@@ -321,7 +321,17 @@ __device__ __forceinline__ void merge_tile_checksum_body(const TileArgs<K>& p, i
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-    if ((tid & 31) == 0 && acc) atomicAdd(sum, (unsigned long long)acc);
+    __syncthreads();  // the index array is free again: reuse it for warp sums
+    uint64_t* wsum = reinterpret_cast<uint64_t*>(lay.sidx);
+    if ((tid & 31) == 0) wsum[tid >> 5] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        uint64_t total = 0;
+        for (int w = 0; w < NT / 32; ++w) total += wsum[w];
+        partial[tile] = total;
+    }
 }
+
+
 
 }  // namespace mp

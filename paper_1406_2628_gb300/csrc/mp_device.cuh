@@ -27,10 +27,13 @@ namespace mp {
 //                  flipped; positives: sign bit set), which orders -0.0
 //                  before +0.0 and keeps IEEE numeric order otherwise.
 // ---------------------------------------------------------------------------
+// Descending order adds inv = all ones: the encoded keys are complemented,
+// so ascending comparison of them is descending order of the keys.
 template <class K>
 struct Codec {
     K flip;
     K fmask;
+    K inv;
 };
 
 template <class K>
@@ -38,7 +41,7 @@ __device__ __forceinline__ K key_enc(K x, Codec<K> c)
 {
     using S = typename std::conditional<sizeof(K) == 8, int64_t, int32_t>::type;
     K fill = (K)((S)x >> (8 * sizeof(K) - 1));
-    return x ^ ((fill & c.fmask) | c.flip);
+    return x ^ ((fill & c.fmask) | c.flip) ^ c.inv;
 }
 
 // Codec kinds known at compile time: identity (unsigned keys: the
@@ -62,6 +65,7 @@ template <class K>
 __device__ __forceinline__ K key_dec(K e, Codec<K> c)
 {
     using S = typename std::conditional<sizeof(K) == 8, int64_t, int32_t>::type;
+    e ^= c.inv;
     K fill = (K)((S)(~e) >> (8 * sizeof(K) - 1));
     return e ^ ((fill & c.fmask) | c.flip);
 }

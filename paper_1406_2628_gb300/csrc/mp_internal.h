@@ -16,6 +16,8 @@ struct KeyKind {
     int bytes;       // 4 or 8
     uint64_t flip;   // top bit for signed and float keys
     uint64_t fmask;  // all ones for float keys
+    uint64_t inv;    // all ones for descending order (MP_DESCENDING)
+    bool identity() const { return flip == 0 && fmask == 0 && inv == 0; }
 };
 bool key_kind(mp_dtype dtype, KeyKind* out);
 
@@ -105,7 +107,7 @@ struct GroupMergeDesc {
     void* out;
     uint32_t* outv;
     int64_t na, nb, run;  // run > 0: sort pass over a[0..na) (see MergeProblem)
-    uint64_t flip, fmask;
+    uint64_t flip, fmask, inv;
 };
 struct GroupSortDesc {
     const void* in;
@@ -113,7 +115,7 @@ struct GroupSortDesc {
     void* out;
     uint32_t* vout;
     int64_t n;
-    uint64_t flip, fmask;
+    uint64_t flip, fmask, inv;
 };
 // tile_first[p]: first tile of problem p (prefix of ceil(total/T));
 // bound_first[p] = tile_first[p] + p; d_splits: total_tiles + nprob int64.
@@ -134,8 +136,10 @@ mp_status check_merge_args_ext(const KeyKind& k, const void* a, const uint32_t* 
 
 // Read-only merge (results folded into a checksum, merge.cu).
 int64_t checksum_tile(int key_bytes, bool vals);
+// partial: one uint64 per tile (scratch), sum: the result word.
 cudaError_t launch_merge_checksum(const MergeProblem& p, const int64_t* a_split,
-                                  unsigned long long* sum, cudaStream_t stream);
+                                  unsigned long long* partial, unsigned long long* sum,
+                                  cudaStream_t stream);
 
 // Device address of the word kernels set when a bounded wait runs out.
 unsigned int* kernel_error_word();

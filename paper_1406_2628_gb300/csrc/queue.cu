@@ -295,14 +295,14 @@ static cudaError_t run_step(mp_queue* q, std::vector<Job*>& work, int slot, uint
         const int v = j->vals ? 1 : 0;
         if (j->req.op == MP_OP_MERGE) {
             GroupMergeDesc d = {j->x, j->b, j->xv, j->bv, j->out, j->outv, j->req.na, j->req.nb, 0,
-                                j->kind.flip, j->kind.fmask};
+                                j->kind.flip, j->kind.fmask, j->kind.inv};
             g.m[w][v].push_back(d);
         } else if (j->stage == 0) {
             // Block sort into the buffer from which an even number of
             // remaining passes ends in X.
             void* dst = (j->passes & 1) ? j->y : j->x;
             uint32_t* dstv = (j->passes & 1) ? j->yv : j->xv;
-            GroupSortDesc d = {j->x, j->xv, dst, dstv, j->n, j->kind.flip, j->kind.fmask};
+            GroupSortDesc d = {j->x, j->xv, dst, dstv, j->n, j->kind.flip, j->kind.fmask, j->kind.inv};
             g.s[w][v].push_back(d);
         } else {
             const int p = j->stage - 1;  // pass index
@@ -312,7 +312,8 @@ static cudaError_t run_step(mp_queue* q, std::vector<Job*>& work, int slot, uint
             void* dst = src_is_y ? j->x : j->y;
             uint32_t* dstv = src_is_y ? j->xv : j->yv;
             GroupMergeDesc d = {src, src, srcv, srcv, dst, dstv, j->n, 0,
-                                grouped_sort_tile(j->kind.bytes) << p, j->kind.flip, j->kind.fmask};
+                                grouped_sort_tile(j->kind.bytes) << p, j->kind.flip, j->kind.fmask,
+                                j->kind.inv};
             g.m[w][v].push_back(d);
         }
     }

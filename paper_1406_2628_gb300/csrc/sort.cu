@@ -74,6 +74,7 @@ static cudaError_t launch_block_sort(const K* in, const uint32_t* vin, K* out, u
     Codec<K> c;
     c.flip = (K)kind.flip;
     c.fmask = (K)kind.fmask;
+    c.inv = (K)kind.inv;
     const int64_t blocks = ceil_div(n, (int64_t)NT * VT);
     kern<<<(unsigned)blocks, NT, SM::bytes, stream>>>(in, vin, out, vout, n, c);
     return cudaGetLastError();
