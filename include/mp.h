@@ -91,13 +91,14 @@ typedef enum mp_dtype {
 typedef struct mp_plan {
     int32_t block_threads;
     int32_t items_per_thread;
-    int32_t staging;  /* MP_STAGE_AUTO, MP_STAGE_VECTOR (128-bit loads) or MP_STAGE_BULK (1D TMA) */
+    int32_t staging;  /* MP_STAGE_AUTO, _VECTOR, _BULK or _WARP (below) */
     int32_t reserved; /* must be 0 */
 } mp_plan;
 
 #define MP_STAGE_AUTO 0
-#define MP_STAGE_VECTOR 1
-#define MP_STAGE_BULK 2
+#define MP_STAGE_VECTOR 1 /* windows via 128-bit loads through registers; per-thread serial merge */
+#define MP_STAGE_BULK 2   /* windows via TMA bulk copies; per-thread serial merge */
+#define MP_STAGE_WARP 3   /* windows via TMA bulk copies; warp-cooperative rank merge */
 
 /* Text for a status code (static storage, never NULL). */
 MP_API const char* mp_status_string(mp_status status);

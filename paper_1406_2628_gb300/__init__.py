@@ -42,7 +42,7 @@ MP_OP_MERGE, MP_OP_SORT = 0, 1
 MP_SRC_HOST, MP_SRC_DEVICE, MP_SRC_GENERATE = 0, 1, 2
 MP_SINK_HOST, MP_SINK_DEVICE, MP_SINK_DISCARD = 0, 1, 2
 
-MP_STAGE_AUTO, MP_STAGE_VECTOR, MP_STAGE_BULK = 0, 1, 2
+MP_STAGE_AUTO, MP_STAGE_VECTOR, MP_STAGE_BULK, MP_STAGE_WARP = 0, 1, 2, 3
 
 _TORCH_DTYPE = {
     torch.int32: MP_I32,

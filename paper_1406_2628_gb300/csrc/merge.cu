@@ -47,6 +47,15 @@ __global__ void __launch_bounds__(NT) merge_tile_kernel(TileArgs<K> p)
     merge_tile_body<K, VALS, NT, VT, CK>(p, blockIdx.x, p.a_split, smem);
 }
 
+// TMA-staged tile merged warp-cooperatively (MP_STAGE_WARP).
+template <class K, bool VALS, int NT, int VT, int CK>
+__global__ void __launch_bounds__(NT) merge_tile_warp_kernel(TileArgs<K> p, unsigned int* err)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    merge_tile_warp_body<K, VALS, NT, VT, CK>(p, blockIdx.x, p.a_split, smem, err);
+}
+
 // Variant whose windows are staged by TMA bulk copies (one tile per CTA).
 template <class K, bool VALS, int NT, int VT, int CK>
 __global__ void __launch_bounds__(NT) merge_tile_bulk_kernel(TileArgs<K> p, unsigned int* err)
@@ -198,6 +207,40 @@ static cudaError_t launch_bulk_ck(const MergeProblem& p, const int64_t* a_split,
     return cudaLaunchKernelEx(&cfg, kern, make_args<K>(p, a_split), err);
 }
 
+template <class K, bool VALS, int NT, int VT, int CK>
+static cudaError_t launch_warp_ck(const MergeProblem& p, const int64_t* a_split, cudaStream_t stream)
+{
+    using SM = WarpSmem<K, VALS, NT, VT>;
+    auto kern = merge_tile_warp_kernel<K, VALS, NT, VT, CK>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    unsigned int* err = kernel_error_word();
+    if (!err) return cudaErrorInvalidSymbol;
+    const int64_t tiles = ceil_div(p.total(), (int64_t)NT * VT);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)tiles);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = SM::bytes;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, make_args<K>(p, a_split), err);
+}
+
+template <class K, bool VALS, int NT, int VT>
+static cudaError_t launch_warp_t(const MergeProblem& p, const int64_t* a_split, cudaStream_t stream)
+{
+    if (p.kind.identity()) return launch_warp_ck<K, VALS, NT, VT, CODEC_IDENTITY>(p, a_split, stream);
+    return launch_warp_ck<K, VALS, NT, VT, CODEC_RUNTIME>(p, a_split, stream);
+}
+
 template <class K, bool VALS, int NT, int VT>
 static cudaError_t launch_bulk_t(const MergeProblem& p, const int64_t* a_split, cudaStream_t stream)
 {
@@ -209,6 +252,7 @@ static cudaError_t launch_bulk_t(const MergeProblem& p, const int64_t* a_split, 
 // Compiled tile shapes (NT, VT): vector staging and TMA bulk staging.
 #define MP_MERGE_SHAPES(X) X(128, 8) X(256, 8) X(128, 16) X(256, 16) X(512, 8)
 #define MP_BULK_SHAPES(X) X(128, 8) X(256, 8) X(128, 16) X(256, 16)
+#define MP_WARP_SHAPES(X) X(128, 8) X(256, 8) X(128, 16) X(256, 16)
 
 bool merge_shape_supported(int key_bytes, bool with_values, const Shape& s)
 {
@@ -219,6 +263,8 @@ bool merge_shape_supported(int key_bytes, bool with_values, const Shape& s)
         MP_MERGE_SHAPES(X)
     } else if (s.staging == MP_STAGE_BULK) {
         MP_BULK_SHAPES(X)
+    } else if (s.staging == MP_STAGE_WARP) {
+        MP_WARP_SHAPES(X)
     }
 #undef X
     return false;
@@ -233,6 +279,9 @@ std::vector<Shape> merge_shapes()
 #define X(NT_, VT_) v.push_back(Shape{NT_, VT_, MP_STAGE_BULK});
     MP_BULK_SHAPES(X)
 #undef X
+    // MP_STAGE_WARP is left out: on every workload measured it ran at less
+    // than half the speed of the thread-serial TMA tile, so tuning it only
+    // costs time.
     return v;
 }
 
@@ -259,6 +308,19 @@ cudaError_t launch_merge_tiles(const MergeProblem& p, const Shape& s, const int6
                                cudaStream_t stream)
 {
     const bool vals = p.vals;
+    if (s.staging == MP_STAGE_WARP) {
+#define X(NT_, VT_)                                                                            \
+        if (s.nt == NT_ && s.vt == VT_) {                                                      \
+            if (p.kind.bytes == 4)                                                             \
+                return vals ? launch_warp_t<uint32_t, true, NT_, VT_>(p, a_split, stream)      \
+                            : launch_warp_t<uint32_t, false, NT_, VT_>(p, a_split, stream);    \
+            return vals ? launch_warp_t<uint64_t, true, NT_, VT_>(p, a_split, stream)          \
+                        : launch_warp_t<uint64_t, false, NT_, VT_>(p, a_split, stream);        \
+        }
+        MP_WARP_SHAPES(X)
+#undef X
+        return cudaErrorInvalidValue;
+    }
     if (s.staging == MP_STAGE_BULK) {
 #define X(NT_, VT_)                                                                            \
         if (s.nt == NT_ && s.vt == VT_) {                                                      \

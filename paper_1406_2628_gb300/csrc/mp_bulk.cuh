@@ -334,4 +334,100 @@ __device__ __forceinline__ void merge_tile_checksum_body(const TileArgs<K>& p, i
 
 
 
+// ---------------------------------------------------------------------------
+// Warp-cooperative tile (staging MP_STAGE_WARP).  After the TMA staging, each
+// warp produces 32*VT consecutive outputs in steps of 32: it loads the next
+// 32 elements of A and of B (consecutive shared addresses, no bank
+// conflicts), ranks every candidate against the other side with warp
+// shuffles (an A element's rank is its lane plus the number of B candidates
+// strictly below it; a B element's is its lane plus the number of A
+// candidates not above it, so ties take A), and writes the candidates whose
+// rank is below 32 straight to their outputs.  By Lemma 16 the next 32
+// outputs of the path lie among those 64 candidates.  Only the warp's first
+// split is found by a diagonal search (Alg. 2), by one lane.
+// ---------------------------------------------------------------------------
+template <class K, bool VALS, int NT, int VT>
+struct WarpSmem {
+    static constexpr int T = NT * VT;
+    static constexpr int EK = 16 / sizeof(K);
+    static constexpr size_t keys_bytes = ((size_t)(T + 3 * EK) * sizeof(K) + 15) / 16 * 16;
+    static constexpr size_t vals_bytes = VALS ? ((size_t)(T + 12) * 4 + 15) / 16 * 16 : 0;
+    static constexpr size_t bytes = keys_bytes + vals_bytes + 16;  // + mbarrier
+};
+
+template <class K, bool VALS, int NT, int VT, int CK>
+__device__ __forceinline__ void merge_tile_warp_body(const TileArgs<K>& p, int64_t tile,
+                                                     const int64_t* a_split, unsigned char* smem,
+                                                     unsigned int* err)
+{
+    using SM = WarpSmem<K, VALS, NT, VT>;
+    constexpr int T = NT * VT;
+    constexpr int W = 32 * VT;  // outputs per warp
+    constexpr unsigned FULL = 0xFFFFFFFFu;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    K* sk = reinterpret_cast<K*>(smem);
+    uint32_t* sv = reinterpret_cast<uint32_t*>(smem + SM::keys_bytes);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::keys_bytes + SM::vals_bytes);
+
+    const TilePlace<K> t = tile_place(p, tile, T, a_split);
+    const auto v = stage_view<K, VALS, NT, VT>(t, sk, sv, nullptr);
+    bulk_init(bar);
+    __syncthreads();
+    if (!bulk_stage<K, VALS, NT, VT>(t, v, bar, 0, err)) return;
+
+    const int la = t.la, lb = t.lb, L = la + lb;
+    const int p0 = warp * W;
+    if (p0 >= L) return;
+    const int pend = p0 + W < L ? p0 + W : L;
+    int a = 0;
+    if (lane == 0) a = smem_diagonal_search_ck<CK>(v.sA, la, v.sB, lb, p0, p.codec);
+    a = __shfl_sync(FULL, a, 0);
+    int b = p0 - a;
+    K* gout = p.out + t.d0;
+    uint32_t* gvout = VALS ? p.outv + t.d0 : nullptr;
+    for (int pos = p0; pos < pend;) {
+        const int n_out = pend - pos < 32 ? pend - pos : 32;
+        const int nav = la - a < 32 ? la - a : 32;
+        const int nbv = lb - b < 32 ? lb - b : 32;
+        const bool va = lane < nav, vb = lane < nbv;
+        const K ra = va ? v.sA[a + lane] : K(0);
+        const K rb = vb ? v.sB[b + lane] : K(0);
+        const K ka = key_enc_ck<CK>(ra, p.codec);
+        const K kb = key_enc_ck<CK>(rb, p.codec);
+        // cnt_b: B candidates strictly below ka; cnt_a: A candidates <= kb.
+        int lo_b = 0, hi_b = nbv, lo_a = 0, hi_a = nav;
+#pragma unroll
+        for (int it = 0; it < 6; ++it) {
+            const int mb = (lo_b + hi_b) >> 1;
+            const int ma = (lo_a + hi_a) >> 1;
+            const K kbm = __shfl_sync(FULL, kb, mb & 31);
+            const K kam = __shfl_sync(FULL, ka, ma & 31);
+            if (lo_b < hi_b) {
+                if (kbm < ka) lo_b = mb + 1;
+                else hi_b = mb;
+            }
+            if (lo_a < hi_a) {
+                if (kam <= kb) lo_a = ma + 1;
+                else hi_a = ma;
+            }
+        }
+        const int r_a = lane + lo_b;
+        const int r_b = lane + lo_a;
+        const bool out_a = va && r_a < n_out;
+        const bool out_b = vb && r_b < n_out;
+        if (out_a) {
+            gout[pos + r_a] = ra;
+            if constexpr (VALS) gvout[pos + r_a] = v.vA[a + lane];
+        }
+        if (out_b) {
+            gout[pos + r_b] = rb;
+            if constexpr (VALS) gvout[pos + r_b] = v.vB[b + lane];
+        }
+        const int taken_a = __popc(__ballot_sync(FULL, out_a));
+        a += taken_a;
+        b += n_out - taken_a;
+        pos += n_out;
+    }
+}
+
 }  // namespace mp

@@ -18,7 +18,9 @@ SIZES = [(0, 0), (1, 0), (0, 1), (1, 1), (5, 3), (4095, 1), (4096, 4096), (12_30
          (70_001, 33_333), (100_000, 0), (0, 65_537), (3, 200_000)]
 PLANS = [(128, 8), (256, 8), (128, 16), (256, 16), (512, 8),
          (128, 8, mp.MP_STAGE_BULK), (256, 8, mp.MP_STAGE_BULK), (128, 16, mp.MP_STAGE_BULK),
-         (256, 16, mp.MP_STAGE_BULK)]
+         (256, 16, mp.MP_STAGE_BULK),
+         (128, 8, mp.MP_STAGE_WARP), (256, 8, mp.MP_STAGE_WARP), (128, 16, mp.MP_STAGE_WARP),
+         (256, 16, mp.MP_STAGE_WARP)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -79,7 +81,8 @@ def test_merge_every_plan(plan, dt):
         assert first_mismatch(to_host(ov, np.uint32), ev) is None
 
 
-@pytest.mark.parametrize("plan", [None, (128, 8, mp.MP_STAGE_BULK), (256, 16, mp.MP_STAGE_BULK)], ids=str)
+@pytest.mark.parametrize("plan", [None, (128, 8, mp.MP_STAGE_BULK), (256, 16, mp.MP_STAGE_BULK),
+                                  (256, 8, mp.MP_STAGE_WARP)], ids=str)
 @pytest.mark.parametrize("dt", [np.int32, np.uint64, np.float32], ids=lambda d: np.dtype(d).name)
 def test_unaligned_pointers(dt, plan):
     """Windows and outputs at every 16-byte phase: sub-views offset by one
@@ -128,7 +131,8 @@ def test_bulk_staging_edge_sizes(dt):
         a, b = random_sorted(rng, dt, na, "ties"), random_sorted(rng, dt, nb, "ties")
         av = np.arange(na, dtype=np.uint32)
         bv = np.arange(na, na + nb, dtype=np.uint32)
-        for plan in [(128, 8, mp.MP_STAGE_BULK), (256, 16, mp.MP_STAGE_BULK)]:
+        for plan in [(128, 8, mp.MP_STAGE_BULK), (256, 16, mp.MP_STAGE_BULK),
+                     (128, 8, mp.MP_STAGE_WARP), (256, 16, mp.MP_STAGE_WARP)]:
             ok, ov = mp.mp_merge_plan(to_dev(a), to_dev(b), vals_to_dev(av), vals_to_dev(bv), plan=plan)
             ek, ev = oracle.merge(a, b, av, bv)
             assert first_mismatch(to_host(ok, dt), ek) is None, (na, nb, plan)
