@@ -12,6 +12,8 @@ compiles that file with gcc, loads it with ctypes and marshals numpy arrays:
 * ``split``          Alg. 2 diagonal intersection -> (a_start, steps)
 * ``sort``           bottom-up merge sort (Sec. I, Sec. III), stable
 * ``merge_batched``  one merge per segment at offset a_off[s]+b_off[s] (Cor. 6)
+* ``set_op``         union / intersection / difference / symmetric difference
+                     of sorted inputs, multiset semantics (merge walk, Sec. I)
 
 Key order: integers natural; float32 numeric with -0.0 before +0.0 (no NaN).
 """
@@ -74,6 +76,9 @@ def load_library(path: str):
         f = getattr(lib, f"oracle_merge_batched_{sfx}")
         f.argtypes = [p, p, p, p, p, p, i64, p, p]
         f.restype = None
+        f = getattr(lib, f"oracle_set_op_{sfx}")
+        f.argtypes = [ctypes.c_int, p, p, i64, p, p, i64, p, p]
+        f.restype = i64
     return lib
 
 
@@ -161,3 +166,23 @@ def merge_batched(a, a_off, b, b_off, av=None, bv=None, lib=None):
         _ptr(a), _ptr(av), _ptr(a_off), _ptr(b), _ptr(bv), _ptr(b_off), nseg,
         _ptr(out), _ptr(outv))
     return out, outv
+
+
+SET_OPS = {"union": 0, "intersection": 1, "difference": 2, "symmetric_difference": 3}
+
+
+def set_op(op, a, b, av=None, bv=None, lib=None):
+    """Set operation ``op`` (a name in SET_OPS or its code) of sorted a and b,
+    multiset semantics; returns (keys, values or None), trimmed to length."""
+    code = SET_OPS[op] if isinstance(op, str) else int(op)
+    a, b = _c(a), _c(b)
+    sfx = _sfx(a, b)
+    pairs = av is not None
+    if pairs != (bv is not None):
+        raise ValueError("give values for both sides or for neither")
+    av, bv = _c(av, np.uint32), _c(bv, np.uint32)
+    out = np.empty(a.size + b.size, dtype=a.dtype)
+    outv = np.empty(a.size + b.size, dtype=np.uint32) if pairs else None
+    k = getattr(lib or _load(), f"oracle_set_op_{sfx}")(code, _ptr(a), _ptr(av), a.size, _ptr(b),
+                                                   _ptr(bv), b.size, _ptr(out), _ptr(outv))
+    return out[:k].copy(), (outv[:k].copy() if pairs else None)

@@ -23,6 +23,18 @@
  *   batched Cor. 6 applied to many independent (A_s, B_s) pairs: each
  *           segment is merged on its own and written at its offset
  *           a_off[s] + b_off[s] of the concatenated output.
+ *   set_op  merge-based set operations (Sec. I names joins of database
+ *           query results and merges of adjacency lists as uses of
+ *           merging).  The same two-pointer walk as the merge, where equal
+ *           heads form a matched pair.  Multiset semantics: a key present
+ *           m times in A and n times in B appears
+ *             union         max(m, n) times: A's m copies, then B's last
+ *                           max(n - m, 0) copies;
+ *             intersection  min(m, n) times: A's first min(m, n) copies;
+ *             difference    max(m - n, 0) times: A's last m - n copies;
+ *             symmetric     |m - n| times: A's last m - n copies, or B's
+ *                           last n - m copies.
+ *           On duplicate-free inputs these are the ordinary set operations.
  *
  * Key order.  Integers use their natural order.  float32 uses the IEEE-754
  * numeric order with -0.0 ordered before +0.0 (NaN is not a valid input).
@@ -59,6 +71,7 @@ static int gt_f32(float x, float y)
  *   oracle_split_<suffix>     Alg. 2 diagonal intersection
  *   oracle_sort_<suffix>      bottom-up merge sort (Sec. I)
  *   oracle_merge_batched_<suffix>  one merge per segment (Cor. 6)
+ *   oracle_set_op_<suffix>    union / intersection / difference / symmetric
  */
 #define ORACLE_TYPE(SFX, T)                                                          \
                                                                                      \
@@ -175,6 +188,58 @@ void oracle_merge_batched_##SFX(const T* a, const uint32_t* av, const int64_t* a
                            b_off[s + 1] - b_off[s],                                  \
                            out + c, outv ? outv + c : NULL);                         \
     }                                                                                \
+}                                                                                    \
+                                                                                     \
+/* Set operation op (0 union, 1 intersection, 2 difference A - B, 3 symmetric   */ \
+/* difference) of sorted A and B.  Emitted keys go to out (values to outv if    */ \
+/* not NULL: an emitted element keeps its own side's value).  Returns the      */ \
+/* number of outputs.  out must hold na + nb keys.                              */ \
+int64_t oracle_set_op_##SFX(int op, const T* a, const uint32_t* av, int64_t na,    \
+                            const T* b, const uint32_t* bv, int64_t nb,            \
+                            T* out, uint32_t* outv)                                \
+{                                                                                    \
+    const int keep_a_alone = (op == 0 || op == 2 || op == 3);                        \
+    const int keep_b_alone = (op == 0 || op == 3);                                   \
+    const int keep_pair = (op == 0 || op == 1);                                      \
+    int64_t i = 0, j = 0, k = 0;                                                     \
+    while (i < na && j < nb) {                                                       \
+        if (gt_##SFX(a[i], b[j])) {          /* B's head is smaller */             \
+            if (keep_b_alone) {                                                      \
+                out[k] = b[j];                                                       \
+                if (outv) outv[k] = bv[j];                                           \
+                k++;                                                                 \
+            }                                                                        \
+            j++;                                                                     \
+        } else if (gt_##SFX(b[j], a[i])) {   /* A's head is smaller */             \
+            if (keep_a_alone) {                                                      \
+                out[k] = a[i];                                                       \
+                if (outv) outv[k] = av[i];                                           \
+                k++;                                                                 \
+            }                                                                        \
+            i++;                                                                     \
+        } else {                             /* equal heads: a matched pair */     \
+            if (keep_pair) {                                                         \
+                out[k] = a[i];                                                       \
+                if (outv) outv[k] = av[i];                                           \
+                k++;                                                                 \
+            }                                                                        \
+            i++;                                                                     \
+            j++;                                                                     \
+        }                                                                            \
+    }                                                                                \
+    for (; i < na; i++)                                                              \
+        if (keep_a_alone) {                                                          \
+            out[k] = a[i];                                                           \
+            if (outv) outv[k] = av[i];                                               \
+            k++;                                                                     \
+        }                                                                            \
+    for (; j < nb; j++)                                                              \
+        if (keep_b_alone) {                                                          \
+            out[k] = b[j];                                                           \
+            if (outv) outv[k] = bv[j];                                               \
+            k++;                                                                     \
+        }                                                                            \
+    return k;                                                                        \
 }
 
 ORACLE_TYPE(i32, int32_t)

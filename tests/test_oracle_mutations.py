@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 import test_oracle_pins as pins
+import test_oracle_setops as setpins
 
 # (name, text in mp_oracle.c, replacement)
 MUTATIONS = [
@@ -41,6 +42,25 @@ MUTATIONS = [
     ("batched writes segments at the A offset only",
      "int64_t c = a_off[s] + b_off[s];",
      "int64_t c = a_off[s] + b_off[s] - (s > 0 && b_off[s] > 0 ? 1 : 0);"),
+    ("set op: symmetric difference keeps matched pairs",
+     "const int keep_pair = (op == 0 || op == 1);",
+     "const int keep_pair = (op == 0 || op == 1 || op == 3);"),
+    ("set op: equal heads treated as B smaller",
+     "if (gt_##SFX(a[i], b[j])) {          /* B's head is smaller */",
+     "if (!gt_##SFX(b[j], a[i])) {          /* B's head is smaller */"),
+    ("set op: a matched pair advances A only",
+     """            i++;                                                                     \\
+            j++;                                                                     \\
+        }                                                                            \\
+    }                                                                                \\
+    for (; i < na; i++)""",
+     """            i++;                                                                     \\
+        }                                                                            \\
+    }                                                                                \\
+    for (; i < na; i++)"""),
+    ("set op: difference keeps B's leftovers",
+     "const int keep_b_alone = (op == 0 || op == 3);",
+     "const int keep_b_alone = (op == 0 || op == 2 || op == 3);"),
 ]
 
 PINS = [
@@ -51,6 +71,9 @@ PINS = [
     pins.test_closed_form_distinct16_groups,
     pins.test_sort_special_orders,
     pins.test_merge_batched_vs_brute_force,
+    setpins.test_set_ops_hand_example,
+    setpins.test_set_ops_cardinality_identities,
+    setpins.test_set_ops_exhaustive_tiny_vs_counting,
 ]
 PINS_DTYPE = [
     pins.test_closed_form_all_equal,
