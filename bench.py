@@ -66,7 +66,7 @@ def parse_args():
     p.add_argument("--plan", default=None, help="NT,VT tile plan (default: automatic)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the other workloads (plain keys, sort, batched, serving)")
-    p.add_argument("--extras", default="plain,sort,batched,serving",
+    p.add_argument("--extras", default="plain,sort,batched,serving,setops",
                    help="comma list of extra workloads to run after the headline")
     p.add_argument("--serving-requests", type=int, default=50000)
     return p.parse_args()
@@ -298,8 +298,64 @@ def extra_plain(mp, torch, dev, reps=50):
         cold.append(e0.elapsed_time(e1) * 1e3)
     n = a.size + b.size
     cold_us = statistics.median(cold)
-    return {"n": n, "warm_us": warm_us, "cold_us": cold_us, "gkeys_s_warm": n / warm_us / 1e3,
-            "gkeys_s_cold": n / cold_us / 1e3, "gbs_cold": 2 * n * 4 / cold_us / 1e3}
+    # The same merge through the partitioned tile path (partition + merge
+    # kernels), which automatic plans use above the streaming threshold.
+    tile = (0, 0, mp.MP_STAGE_BULK)
+    tcold = []
+    for _ in range(reps // 2):
+        flush.fill_(1)
+        e0.record()
+        mp.mp_merge_plan(A, B, out_keys=out, plan=tile)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        tcold.append(e0.elapsed_time(e1) * 1e3)
+    return {"n": n, "call": "mp_merge_keys (automatic plan: streaming merge, one launch)",
+            "warm_us": warm_us, "cold_us": cold_us, "gkeys_s_warm": n / warm_us / 1e3,
+            "gkeys_s_cold": n / cold_us / 1e3, "gbs_cold": 2 * n * 4 / cold_us / 1e3,
+            "partitioned_cold_us": statistics.median(tcold)}
+
+
+def extra_setops(mp, torch, dev, log2_universe=28, reps=5):
+    """Set operations on two duplicate-free sorted sets of ~2^27 uint32 keys,
+    each key of [0, 2^28) in each set with probability 1/2 (independent), so
+    about half of each set is in the other; keys only, and union with values."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(0x14062628)
+    u = 1 << log2_universe
+    A = torch.nonzero(torch.rand(u, device=dev, generator=g) < 0.5).flatten().to(torch.int32)
+    B = torch.nonzero(torch.rand(u, device=dev, generator=g) < 0.5).flatten().to(torch.int32)
+    na, nb = A.numel(), B.numel()
+    out = torch.empty(na + nb, dtype=torch.int32, device=dev)
+    cnt = torch.empty(1, dtype=torch.int64, device=dev)
+    res = {"na": na, "nb": nb, "key": "uint32 (as int32 < 2^28)"}
+    e0, e1 = _events(torch)
+    for op in ["union", "intersection", "difference", "symmetric_difference"]:
+        mp.mp_set_operation(op, A, B, out_keys=out, count=cnt, trim=False)
+        torch.cuda.synchronize(dev)
+        e0.record()
+        for _ in range(reps):
+            mp.mp_set_operation(op, A, B, out_keys=out, count=cnt, trim=False)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        k = int(cnt.item())
+        res[op] = {"ms": ms, "out": k, "gkeys_s": (na + nb) / ms / 1e6,
+                   "gbs": (na + nb + k) * 4 / ms / 1e6}
+    AV = torch.arange(na, dtype=torch.int32, device=dev)
+    BV = torch.arange(nb, dtype=torch.int32, device=dev)
+    OV = torch.empty(na + nb, dtype=torch.int32, device=dev)
+    mp.mp_set_operation("union", A, B, AV, BV, out, OV, count=cnt, trim=False)
+    torch.cuda.synchronize(dev)
+    e0.record()
+    for _ in range(reps):
+        mp.mp_set_operation("union", A, B, AV, BV, out, OV, count=cnt, trim=False)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    k = int(cnt.item())
+    res["union_pairs"] = {"ms": ms, "out": k, "gkeys_s": (na + nb) / ms / 1e6,
+                          "gbs": (na + nb + k) * 8 / ms / 1e6}
+    return res
 
 
 def _device_sort_input(torch, dev, dtype, order, n, seed):
@@ -704,7 +760,8 @@ def run_ours(args):
         runners = {"plain": lambda: extra_plain(mp, torch, dev),
                    "sort": lambda: extra_sort(mp, torch, dev),
                    "batched": lambda: extra_batched(mp, torch, dev),
-                   "serving": lambda: extra_serving(mp, torch, dev, n_req=args.serving_requests)}
+                   "serving": lambda: extra_serving(mp, torch, dev, n_req=args.serving_requests),
+                   "setops": lambda: extra_setops(mp, torch, dev)}
         del OK, OV
         for name in wanted:
             t0 = time.perf_counter()

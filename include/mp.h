@@ -91,7 +91,7 @@ typedef enum mp_dtype {
 typedef struct mp_plan {
     int32_t block_threads;
     int32_t items_per_thread;
-    int32_t staging;  /* MP_STAGE_AUTO, _VECTOR, _BULK or _WARP (below) */
+    int32_t staging;  /* MP_STAGE_AUTO, _VECTOR, _BULK, _WARP or _STREAM (below) */
     int32_t reserved; /* must be 0 */
 } mp_plan;
 
@@ -99,6 +99,14 @@ typedef struct mp_plan {
 #define MP_STAGE_VECTOR 1 /* windows via 128-bit loads through registers; per-thread serial merge */
 #define MP_STAGE_BULK 2   /* windows via TMA bulk copies; per-thread serial merge */
 #define MP_STAGE_WARP 3   /* windows via TMA bulk copies; warp-cooperative rank merge */
+/* Partition-free streaming merge (Alg. 3): one launch, no split-point
+ * array.  Each CTA owns R consecutive tiles of the output, finds the splits
+ * at both ends of its share (Alg. 2, one warp per end), then walks its share
+ * tile by tile, carrying the path position; A and B stream through
+ * shared-memory ring buffers filled by TMA bulk copies a few tiles ahead.
+ * Plain merges only (mp_merge_keys/_pairs/_plan, graphs); mp_merge_partitioned
+ * rejects it (it takes no split points). */
+#define MP_STAGE_STREAM 4
 
 /* Text for a status code (static storage, never NULL). */
 MP_API const char* mp_status_string(mp_status status);
@@ -115,7 +123,9 @@ MP_API size_t mp_dtype_size(mp_dtype dtype);
  *   must not overlap a or b.  na = nb = 0 is a no-op.  Ties take A first.
  * Runs a partition kernel (Alg. 2 at every tile boundary, Thm 9 / Thm 14)
  * and a merge kernel (one tile per CTA, Cor. 6).  Scratch: (tiles+1) int64
- * split points from the library pool.
+ * split points from the library pool.  Small merges (up to a few million
+ * outputs) take the single-launch streaming merge instead (MP_STAGE_STREAM,
+ * no scratch) unless the tuned table says otherwise.
  */
 MP_API mp_status mp_merge_keys(mp_dtype dtype, const void* a, int64_t na,
                         const void* b, int64_t nb, void* out, mp_stream_t stream);
@@ -160,8 +170,10 @@ MP_API int mp_plan_supported(const mp_plan* plan);
 
 /*
  * mp_merge_tile_items -- the tile length T (outputs per CTA) that
- * mp_merge_plan / mp_merge_partitioned use for this dtype, payload choice,
- * total output length and plan (NULL = automatic).  0 if the plan is not
+ * mp_merge_partitioned uses for this dtype, payload choice, total output
+ * length and plan (NULL = automatic; the automatic choice here is always a
+ * partitioned tile plan, while an automatic mp_merge_plan / mp_merge_keys
+ * may take the streaming plan for small merges).  0 if the plan is not
  * supported or the dtype unknown.
  */
 MP_API int64_t mp_merge_tile_items(mp_dtype dtype, int with_values, int64_t total,
@@ -215,6 +227,54 @@ MP_API mp_status mp_merge_checksum(mp_dtype dtype,
                                    const void* a_keys, const uint32_t* a_vals, int64_t na,
                                    const void* b_keys, const uint32_t* b_vals, int64_t nb,
                                    uint64_t* checksum, mp_stream_t stream);
+
+/*
+ * Merge-based set operations.  Sec. I names joins of database query results
+ * and merges of adjacency lists as uses of merging; these are the merge with
+ * a keep-or-drop decision per output.  Multiset semantics: a key held m
+ * times by A and n times by B appears
+ *   MP_SET_UNION                 max(m, n) times: A's m copies, then B's
+ *                                copies after the m-th;
+ *   MP_SET_INTERSECTION          min(m, n) times: A's first min(m, n) copies;
+ *   MP_SET_DIFFERENCE            max(m - n, 0) times: A's copies after the
+ *                                n-th (A minus B);
+ *   MP_SET_SYMMETRIC_DIFFERENCE  |m - n| times: A's copies after the n-th or
+ *                                B's copies after the m-th.
+ * On duplicate-free inputs these are the ordinary set operations.  Output is
+ * ascending (descending with MP_DESCENDING), equal keys keep merge order (A's
+ * copies before B's), and every emitted element carries its own value.
+ */
+typedef enum mp_setop {
+    MP_SET_UNION = 0,
+    MP_SET_INTERSECTION = 1,
+    MP_SET_DIFFERENCE = 2,
+    MP_SET_SYMMETRIC_DIFFERENCE = 3
+} mp_setop;
+
+/* Output capacity (elements) mp_set_operation needs: na + nb for union and
+ * symmetric difference, min(na, nb) for intersection, na for difference;
+ * -1 for an unknown op or a negative size. */
+MP_API int64_t mp_set_capacity(mp_setop op, int64_t na, int64_t nb);
+
+/*
+ * mp_set_operation -- set operation `op` of sorted A and B.
+ *   a_keys[0..na), b_keys[0..nb): sorted, device.  out_keys (and out_vals
+ *   when values are given: any of a_vals, b_vals, out_vals non-NULL) hold
+ *   mp_set_capacity(op, na, nb) elements, device, not overlapping an input.
+ *   out_count: device pointer to one int64, set to the result length.
+ * One partition kernel (Alg. 2 at every tile boundary, Cor. 6) and one
+ * kernel that merges each tile, decides each output, and writes the kept
+ * ones contiguously (a block scan inside the tile, a decoupled look-back
+ * across tiles, so the inputs are read once).  Scratch from the library
+ * pool: split points and one status word per tile.  Asynchronous; inputs
+ * that are not sorted give an unspecified subsequence and, where a tile's
+ * output would pass the capacity, set bit 2 of mp_kernel_error().
+ */
+MP_API mp_status mp_set_operation(mp_setop op, mp_dtype dtype,
+                                  const void* a_keys, const uint32_t* a_vals, int64_t na,
+                                  const void* b_keys, const uint32_t* b_vals, int64_t nb,
+                                  void* out_keys, uint32_t* out_vals, int64_t* out_count,
+                                  mp_stream_t stream);
 
 /*
  * mp_sort_workspace_bytes -- device workspace that mp_sort needs for n keys
@@ -324,8 +384,10 @@ MP_API mp_status mp_graph_destroy(mp_graph* graph);
 
 /*
  * mp_kernel_error -- SYNCHRONOUS (waits for the device).  Bit flags set by
- * kernels whose bounded waits ran out (1: an mbarrier wait of the TMA-staged
- * merge timed out; the CTA stopped early and its tiles are incomplete).
+ * kernels whose bounded waits ran out (1: an mbarrier wait of a TMA-staged
+ * merge timed out; the CTA stopped early and its tiles are incomplete;
+ * 2: a set operation's tile could not place its output: the look-back over
+ * earlier tiles ran out, or the output would pass the capacity).
  * 0 means no kernel reported a problem since the last reset.  reset != 0
  * clears the flags after reading them.
  */

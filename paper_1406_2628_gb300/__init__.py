@@ -42,7 +42,11 @@ MP_OP_MERGE, MP_OP_SORT = 0, 1
 MP_SRC_HOST, MP_SRC_DEVICE, MP_SRC_GENERATE = 0, 1, 2
 MP_SINK_HOST, MP_SINK_DEVICE, MP_SINK_DISCARD = 0, 1, 2
 
-MP_STAGE_AUTO, MP_STAGE_VECTOR, MP_STAGE_BULK, MP_STAGE_WARP = 0, 1, 2, 3
+MP_STAGE_AUTO, MP_STAGE_VECTOR, MP_STAGE_BULK, MP_STAGE_WARP, MP_STAGE_STREAM = 0, 1, 2, 3, 4
+
+MP_SET_UNION, MP_SET_INTERSECTION, MP_SET_DIFFERENCE, MP_SET_SYMMETRIC_DIFFERENCE = 0, 1, 2, 3
+_SET_OPS = {"union": MP_SET_UNION, "intersection": MP_SET_INTERSECTION,
+            "difference": MP_SET_DIFFERENCE, "symmetric_difference": MP_SET_SYMMETRIC_DIFFERENCE}
 
 _TORCH_DTYPE = {
     torch.int32: MP_I32,
@@ -135,6 +139,8 @@ _SIGNATURES = {
     "mp_queue_get_stats": ([_P, ctypes.POINTER(mp_queue_stats)], _I32),
     "mp_queue_destroy": ([_P], _I32),
     "mp_generate": ([_I32, _P, _P, _I64, ctypes.c_uint64, ctypes.c_uint64, _I32, ctypes.c_uint32, _P], _I32),
+    "mp_set_capacity": ([_I32, _I64, _I64], _I64),
+    "mp_set_operation": ([_I32, _I32, _P, _P, _I64, _P, _P, _I64, _P, _P, _P, _P], _I32),
 }
 
 
@@ -276,6 +282,41 @@ def mp_merge_checksum(a_keys, b_keys, a_vals=None, b_vals=None, out=None, stream
                                    _dev(b_keys, "b_keys"), _vals(b_vals, "b_vals") if pairs else None,
                                    b_keys.numel(), _dev(out, "checksum"), _stream(stream)))
     return out
+
+
+def mp_set_capacity(op, na: int, nb: int) -> int:
+    code = _SET_OPS[op] if isinstance(op, str) else int(op)
+    return int(lib().mp_set_capacity(code, int(na), int(nb)))
+
+
+def mp_set_operation(op, a_keys, b_keys, a_vals=None, b_vals=None, out_keys=None, out_vals=None,
+                     count=None, stream=None, descending: bool = False, trim: bool = True):
+    """Set operation ``op`` ("union", "intersection", "difference",
+    "symmetric_difference" or an MP_SET_* code) of sorted a_keys and b_keys
+    (multiset semantics).  Returns (keys, values or None, count tensor); with
+    trim=True the outputs are sliced to the result length (one device read)."""
+    code = _SET_OPS[op] if isinstance(op, str) else int(op)
+    cap = mp_set_capacity(code, a_keys.numel(), b_keys.numel())
+    if cap < 0:
+        raise MPError(MP_ERR_INVALID_ARG, f"unknown set operation {op!r}")
+    if out_keys is None:
+        out_keys = torch.empty(cap, dtype=a_keys.dtype, device=a_keys.device)
+    pairs = a_vals is not None
+    if pairs and out_vals is None:
+        out_vals = torch.empty(cap, dtype=a_vals.dtype, device=a_keys.device)
+    if count is None:
+        count = torch.empty(1, dtype=torch.int64, device=a_keys.device)
+    _check(lib().mp_set_operation(code, _dtype_code(a_keys, descending), _dev(a_keys, "a_keys"),
+                                  _vals(a_vals, "a_vals") if pairs else None, a_keys.numel(),
+                                  _dev(b_keys, "b_keys"), _vals(b_vals, "b_vals") if pairs else None,
+                                  b_keys.numel(), _dev(out_keys, "out_keys"),
+                                  _vals(out_vals, "out_vals") if pairs else None, _dev(count, "count"),
+                                  _stream(stream)))
+    if trim:
+        n = int(count.item())
+        out_keys = out_keys[:n]
+        out_vals = out_vals[:n] if pairs else None
+    return out_keys, (out_vals if pairs else None), count
 
 
 def mp_merge_tile_items(dtype, with_values: bool, total: int, plan=None) -> int:

@@ -100,26 +100,28 @@ static bool overlaps(const void* p, size_t pb, const void* q, size_t qb)
     return a < b + qb && b < a + pb;
 }
 
+// out_n: the output length in elements (-1: na + nb).
 static mp_status check_merge_args(const KeyKind& k, const void* a, const uint32_t* av, int64_t na,
                                   const void* b, const uint32_t* bv, int64_t nb, const void* out,
-                                  const uint32_t* outv, bool vals, const char* fn)
+                                  const uint32_t* outv, bool vals, const char* fn, int64_t out_n = -1)
 {
     std::string f(fn);
     if (na < 0 || nb < 0) return fail(MP_ERR_INVALID_ARG, f + ": negative size");
     if (na > ((int64_t)1 << 46) || nb > ((int64_t)1 << 46)) return fail(MP_ERR_INVALID_ARG, f + ": size too large");
-    if (vals && ((na > 0 && !av) || (nb > 0 && !bv) || (na + nb > 0 && !outv)))
+    const int64_t on = out_n < 0 ? na + nb : out_n;
+    if (vals && ((na > 0 && !av) || (nb > 0 && !bv) || (on > 0 && !outv)))
         return fail(MP_ERR_INVALID_ARG, f + ": NULL value array for a non-empty side");
-    if ((na > 0 && !a) || (nb > 0 && !b) || (na + nb > 0 && !out))
+    if ((na > 0 && !a) || (nb > 0 && !b) || (on > 0 && !out))
         return fail(MP_ERR_INVALID_ARG, f + ": NULL key pointer");
     if (!aligned(a, k.bytes) || !aligned(b, k.bytes) || !aligned(out, k.bytes))
         return fail(MP_ERR_INVALID_ARG, f + ": key pointer not aligned to the key size");
     if (vals && (!aligned(av, 4) || !aligned(bv, 4) || !aligned(outv, 4)))
         return fail(MP_ERR_INVALID_ARG, f + ": value pointer not 4-byte aligned");
-    const size_t ob = (size_t)(na + nb) * k.bytes;
+    const size_t ob = (size_t)on * k.bytes;
     if (overlaps(out, ob, a, (size_t)na * k.bytes) || overlaps(out, ob, b, (size_t)nb * k.bytes))
         return fail(MP_ERR_INVALID_ARG, f + ": output overlaps an input");
     if (vals) {
-        const size_t ovb = (size_t)(na + nb) * 4;
+        const size_t ovb = (size_t)on * 4;
         if (overlaps(outv, ovb, av, (size_t)na * 4) || overlaps(outv, ovb, bv, (size_t)nb * 4) ||
             overlaps(outv, ovb, out, ob) || overlaps(outv, ovb, a, (size_t)na * k.bytes) ||
             overlaps(outv, ovb, b, (size_t)nb * k.bytes) || overlaps(out, ob, av, (size_t)na * 4) ||
@@ -131,14 +133,33 @@ static mp_status check_merge_args(const KeyKind& k, const void* a, const uint32_
 
 mp_status check_merge_args_ext(const KeyKind& k, const void* a, const uint32_t* av, int64_t na,
                                const void* b, const uint32_t* bv, int64_t nb, const void* out,
-                               const uint32_t* outv, bool vals, const char* fn)
+                               const uint32_t* outv, bool vals, const char* fn, int64_t out_n)
 {
-    return check_merge_args(k, a, av, na, b, bv, nb, out, outv, vals, fn);
+    return check_merge_args(k, a, av, na, b, bv, nb, out, outv, vals, fn, out_n);
 }
 
-static mp_status resolve_shape(const KeyKind& k, bool vals, int64_t total, const mp_plan* plan, Shape* s)
+static bool plan_is_auto(const mp_plan* plan)
 {
+    return !plan || (!plan->block_threads && !plan->items_per_thread && !plan->staging && !plan->reserved);
+}
+
+// allow_stream: an automatic plan may pick the streaming merge (small
+// merges, where it saves the partition launch); callers that supply split
+// points pass false.
+static mp_status resolve_shape(const KeyKind& k, bool vals, int64_t total, const mp_plan* plan, Shape* s,
+                               bool allow_stream = true)
+{
+    if (plan_is_auto(plan)) {
+        if (tuned_shape("merge", k.bytes, vals, total, s) && (allow_stream || s->staging != MP_STAGE_STREAM))
+            return MP_OK;
+        if (allow_stream && total <= stream_auto_limit(k.bytes, vals)) {
+            *s = stream_default_shape(k.bytes, vals);
+            return MP_OK;
+        }
+    }
     *s = default_merge_shape(k.bytes, vals, total);
+    if (s->staging == MP_STAGE_STREAM) *s = Shape{256, 8, MP_STAGE_BULK};  // tuned, but splits are given
+    if (plan && plan->staging == MP_STAGE_STREAM) *s = stream_default_shape(k.bytes, vals);
     if (plan) {
         if (plan->reserved != 0) return fail(MP_ERR_INVALID_ARG, "plan.reserved must be 0");
         if (plan->block_threads) s->nt = plan->block_threads;
@@ -150,20 +171,23 @@ static mp_status resolve_shape(const KeyKind& k, bool vals, int64_t total, const
             s->staging = MP_STAGE_VECTOR;
         }
     }
-    if (!merge_shape_supported(k.bytes, vals, *s))
+    const bool ok = s->staging == MP_STAGE_STREAM ? stream_shape_supported(*s)
+                                                  : merge_shape_supported(k.bytes, vals, *s);
+    if (!ok)
         return fail(MP_ERR_INVALID_ARG, "unsupported merge plan (block_threads, items_per_thread, staging)");
     return MP_OK;
 }
 
 mp_status merge_prepare(mp_dtype dtype, const void* a, const uint32_t* av, int64_t na,
                         const void* b, const uint32_t* bv, int64_t nb, void* out, uint32_t* outv,
-                        bool vals, const mp_plan* plan, const char* fn, MergeProblem* p, Shape* s)
+                        bool vals, const mp_plan* plan, const char* fn, MergeProblem* p, Shape* s,
+                        bool allow_stream)
 {
     KeyKind k;
     if (!key_kind(dtype, &k)) return fail(MP_ERR_UNSUPPORTED_DTYPE, std::string(fn) + ": unknown dtype");
     mp_status st = check_merge_args(k, a, av, na, b, bv, nb, out, outv, vals, fn);
     if (st != MP_OK) return st;
-    st = resolve_shape(k, vals, na + nb, plan, s);
+    st = resolve_shape(k, vals, na + nb, plan, s, allow_stream);
     if (st != MP_OK) return st;
     p->kind = k;
     p->vals = vals;
@@ -186,9 +210,16 @@ static mp_status merge_impl(mp_dtype dtype, const void* a, const uint32_t* av, i
 {
     MergeProblem p;
     Shape s;
-    mp_status st = merge_prepare(dtype, a, av, na, b, bv, nb, out, outv, vals, plan, fn, &p, &s);
+    mp_status st = merge_prepare(dtype, a, av, na, b, bv, nb, out, outv, vals, plan, fn, &p, &s,
+                                 given_splits == nullptr);
     if (st != MP_OK) return st;
+    if (s.staging == MP_STAGE_STREAM && given_splits)
+        return fail(MP_ERR_INVALID_ARG, std::string(fn) + ": the streaming plan takes no split points");
     if (na + nb == 0) return MP_OK;
+    if (s.staging == MP_STAGE_STREAM) {
+        cudaError_t e = launch_merge_stream(p, s, stream);
+        return e == cudaSuccess ? MP_OK : cuda_fail(e, fn);
+    }
     if (given_splits) {
         if (((uintptr_t)given_splits & 7) != 0)
             return fail(MP_ERR_INVALID_ARG, std::string(fn) + ": a_split not 8-byte aligned");
@@ -282,6 +313,7 @@ int mp_plan_supported(const mp_plan* plan)
     if (!plan || plan->reserved) return 0;
     Shape s{plan->block_threads, plan->items_per_thread,
             plan->staging ? plan->staging : MP_STAGE_VECTOR};
+    if (s.staging == MP_STAGE_STREAM) return stream_shape_supported(s) ? 1 : 0;
     return merge_shape_supported(4, false, s) ? 1 : 0;
 }
 
@@ -290,7 +322,7 @@ int64_t mp_merge_tile_items(mp_dtype dtype, int with_values, int64_t total, cons
     KeyKind k;
     if (!key_kind(dtype, &k)) return 0;
     Shape s;
-    if (resolve_shape(k, with_values != 0, total, plan, &s) != MP_OK) return 0;
+    if (resolve_shape(k, with_values != 0, total, plan, &s, false) != MP_OK) return 0;
     return s.tile();
 }
 

@@ -1,6 +1,7 @@
 // graph.cu -- CUDA-graph objects for repeated merges.
 //
-// A merge is two launches (partition, then merge tiles) plus scratch; a
+// A merge is two launches (partition, then merge tiles) plus scratch (one
+// launch and no scratch with the streaming plan); a
 // caller that repeats the same merge on the same buffers (a batched merge
 // over fixed segment offsets, a pipeline stage) can capture it once and
 // replay it with one cudaGraphLaunch.  The graph owns its scratch (split
@@ -62,10 +63,12 @@ mp_status mp_graph_merge_create(mp_dtype dtype, const void* a_keys, const uint32
     mp_status st = merge_prepare(dtype, a_keys, a_vals, na, b_keys, b_vals, nb, out_keys, out_vals, vals,
                                  plan, "mp_graph_merge_create", &p, &s);
     if (st != MP_OK) return st;
-    const int64_t bounds = ceil_div(na + nb, s.tile()) + 1;
+    const bool streaming = s.staging == MP_STAGE_STREAM;
+    const int64_t bounds = streaming ? 0 : ceil_div(na + nb, s.tile()) + 1;
     return capture(
         [&](void* scratch, cudaStream_t cs) -> cudaError_t {
             if (na + nb == 0) return cudaSuccess;
+            if (streaming) return launch_merge_stream(p, s, cs);
             cudaError_t e = launch_partition(p, s.tile(), (int64_t*)scratch, cs);
             if (e == cudaSuccess) e = launch_merge_tiles(p, s, (const int64_t*)scratch, cs);
             return e;

@@ -25,7 +25,7 @@ bool key_kind(mp_dtype dtype, KeyKind* out);
 struct Shape {
     int nt;
     int vt;
-    int staging;  // MP_STAGE_VECTOR or MP_STAGE_BULK
+    int staging;  // MP_STAGE_VECTOR, _BULK, _WARP or _STREAM
     int64_t tile() const { return (int64_t)nt * vt; }
 };
 
@@ -58,6 +58,13 @@ cudaError_t launch_partition(const MergeProblem& p, int64_t spacing, int64_t* a_
 cudaError_t launch_merge_tiles(const MergeProblem& p, const Shape& shape, const int64_t* a_split,
                                cudaStream_t stream);
 bool merge_shape_supported(int key_bytes, bool with_values, const Shape& shape);
+// Partition-free streaming merge (stream.cu): one launch, no scratch.
+cudaError_t launch_merge_stream(const MergeProblem& p, const Shape& shape, cudaStream_t stream);
+bool stream_shape_supported(const Shape& shape);
+std::vector<Shape> stream_shapes();
+// Automatic plans use the streaming merge up to this many outputs.
+int64_t stream_auto_limit(int key_bytes, bool with_values);
+Shape stream_default_shape(int key_bytes, bool with_values);
 Shape default_merge_shape(int key_bytes, bool with_values, int64_t total);
 std::vector<Shape> merge_shapes();
 
@@ -90,7 +97,8 @@ cudaError_t batched_launch(const BatchedProblem& q, const Shape& s, void* scratc
 // Plain merge: validation, then launch with caller scratch (split points).
 mp_status merge_prepare(mp_dtype dtype, const void* a, const uint32_t* av, int64_t na,
                         const void* b, const uint32_t* bv, int64_t nb, void* out, uint32_t* outv,
-                        bool vals, const mp_plan* plan, const char* fn, MergeProblem* p, Shape* s);
+                        bool vals, const mp_plan* plan, const char* fn, MergeProblem* p, Shape* s,
+                        bool allow_stream = true);
 
 // Merge sort.
 size_t sort_workspace_bytes(const KeyKind& kind, int64_t n, bool with_values);
@@ -132,7 +140,13 @@ int64_t grouped_sort_tile(int key_bytes);
 // Merge argument checks (api.cu).
 mp_status check_merge_args_ext(const KeyKind& k, const void* a, const uint32_t* av, int64_t na,
                                const void* b, const uint32_t* bv, int64_t nb, const void* out,
-                               const uint32_t* outv, bool vals, const char* fn);
+                               const uint32_t* outv, bool vals, const char* fn, int64_t out_n = -1);
+
+// Merge-based set operations (setops.cu): splits from launch_partition with
+// spacing setop_tile(); status (one word per tile) and counter zeroed.
+int64_t setop_tile();
+cudaError_t launch_setop(const MergeProblem& p, int op, const int64_t* splits, unsigned long long* status,
+                         unsigned int* counter, int64_t cap, int64_t* count, cudaStream_t stream);
 
 // Read-only merge (results folded into a checksum, merge.cu).
 int64_t checksum_tile(int key_bytes, bool vals);

@@ -117,7 +117,9 @@ mp_status mp_autotune_merge(mp_dtype dtype, const void* a_keys, const uint32_t* 
         return fail(MP_ERR_CUDA, "mp_autotune_merge: events");
     Shape best_s{0, 0, 0};
     float best_ms = 1e30f;
-    for (const Shape& cand : merge_shapes()) {
+    std::vector<Shape> cands = merge_shapes();
+    for (const Shape& c : stream_shapes()) cands.push_back(c);
+    for (const Shape& cand : cands) {
         mp_plan p{cand.nt, cand.vt, cand.staging, 0};
         // Warm-up (also sets kernel attributes), then the fastest of reps.
         st = mp_merge_plan(dtype, a_keys, a_vals, na, b_keys, b_vals, nb, out_keys, out_vals, &p, stream);

@@ -29,7 +29,9 @@ def test_autotune_merge_records_a_compiled_plan(tmp_path):
     default_tile = mp.mp_merge_tile_items(torch.uint64, True, n)
     nt, vt, stg = mp.mp_autotune_merge(A, B, AV, BV, reps=2)
     assert mp.mp_plan_supported((nt, vt, stg))
-    assert mp.mp_merge_tile_items(torch.uint64, True, n) == nt * vt
+    # A streaming winner uses no split points, so the partitioned tile stays.
+    tuned_tile = default_tile if stg == mp.MP_STAGE_STREAM else nt * vt
+    assert mp.mp_merge_tile_items(torch.uint64, True, n) == tuned_tile
     # Automatic plans now use the tuned shape and still merge exactly.
     ok, ov = mp.mp_merge_pairs(A, AV, B, BV)
     ek, ev = oracle.merge(a, b, av, bv)
@@ -41,7 +43,7 @@ def test_autotune_merge_records_a_compiled_plan(tmp_path):
     mp.mp_tune_clear()
     assert mp.mp_merge_tile_items(torch.uint64, True, n) == default_tile
     mp.mp_tune_load(path)
-    assert mp.mp_merge_tile_items(torch.uint64, True, n) == nt * vt
+    assert mp.mp_merge_tile_items(torch.uint64, True, n) == tuned_tile
 
 
 def test_autotune_batched():
