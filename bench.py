@@ -66,7 +66,7 @@ def parse_args():
     p.add_argument("--plan", default=None, help="NT,VT tile plan (default: automatic)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the other workloads (plain keys, sort, batched, serving)")
-    p.add_argument("--extras", default="plain,sort,batched,serving,setops",
+    p.add_argument("--extras", default="plain,sort,batched,serving,setops,wide",
                    help="comma list of extra workloads to run after the headline")
     p.add_argument("--serving-requests", type=int, default=50000)
     return p.parse_args()
@@ -313,6 +313,50 @@ def extra_plain(mp, torch, dev, reps=50):
             "warm_us": warm_us, "cold_us": cold_us, "gkeys_s_warm": n / warm_us / 1e3,
             "gkeys_s_cold": n / cold_us / 1e3, "gbs_cold": 2 * n * 4 / cold_us / 1e3,
             "partitioned_cold_us": statistics.median(tcold)}
+
+
+def extra_wide(mp, torch, dev, log2_n=25, reps=5):
+    """128-bit keys (two 64-bit words, low first), unsigned: merge of two
+    sorted arrays of 2^25 keys each (uniform random words), and a sort of
+    2^25 random keys.  Inputs are made sorted on the device with mp_sort
+    (outside the timed region)."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(0x1406_2628)
+    n = 1 << log2_n
+    lo, hi = -(1 << 63), (1 << 63) - 1
+
+    def rand_keys():
+        return torch.randint(lo, hi, (n, 2), dtype=torch.int64, device=dev, generator=g)
+    A, B = rand_keys(), rand_keys()
+    mp.mp_sort(A, wide="u128")
+    mp.mp_sort(B, wide="u128")
+    out = torch.empty((2 * n, 2), dtype=torch.int64, device=dev)
+    res = {"n_a": n, "n_b": n, "key": "uint128 (2 x uint64, low word first)"}
+    e0, e1 = _events(torch)
+    for name, plan in [("merge_auto", None), ("merge_stream", (128, 8, mp.MP_STAGE_STREAM))]:
+        mp.mp_merge_plan(A, B, out_keys=out, plan=plan, wide="u128")
+        torch.cuda.synchronize(dev)
+        e0.record()
+        for _ in range(reps):
+            mp.mp_merge_plan(A, B, out_keys=out, plan=plan, wide="u128")
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"ms": ms, "gkeys_s": 2 * n / ms / 1e6, "gbs": 2 * 2 * n * 16 / ms / 1e6}
+    X = rand_keys()
+    W = torch.empty(mp.mp_sort_workspace_bytes(mp.MP_U128, n, False), dtype=torch.uint8, device=dev)
+    ts = []
+    for _ in range(3):
+        Y = X.clone()
+        torch.cuda.synchronize(dev)
+        e0.record()
+        mp.mp_sort(Y, workspace=W, wide="u128")
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    res["sort"] = {"n": n, "ms": ms, "gkeys_s": n / ms / 1e6}
+    return res
 
 
 def extra_setops(mp, torch, dev, log2_universe=28, reps=5):
@@ -761,7 +805,8 @@ def run_ours(args):
                    "sort": lambda: extra_sort(mp, torch, dev),
                    "batched": lambda: extra_batched(mp, torch, dev),
                    "serving": lambda: extra_serving(mp, torch, dev, n_req=args.serving_requests),
-                   "setops": lambda: extra_setops(mp, torch, dev)}
+                   "setops": lambda: extra_setops(mp, torch, dev),
+                   "wide": lambda: extra_wide(mp, torch, dev)}
         del OK, OV
         for name in wanted:
             t0 = time.perf_counter()

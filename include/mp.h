@@ -74,7 +74,15 @@ typedef enum mp_dtype {
     MP_U32 = 1, /* uint32_t */
     MP_F32 = 2, /* float (IEEE-754 binary32), -0.0 < +0.0, no NaN */
     MP_U64 = 3, /* uint64_t */
-    MP_I64 = 4  /* int64_t  */
+    MP_I64 = 4, /* int64_t  */
+    /* Multi-word keys: 128-bit integers, two 64-bit words per key, the low
+     * word first in memory (little-endian), 16-byte aligned.  Supported by
+     * the plain merges (tile plans MP_STAGE_BULK (128,8) / (256,8) and the
+     * streaming plans), mp_merge_path_partition, mp_sort, mp_set_operation
+     * and mp_check_sorted; the batched, grouped, queued, checksum and
+     * allocation-free entry points return MP_ERR_UNSUPPORTED_DTYPE. */
+    MP_U128 = 5, /* unsigned 128-bit */
+    MP_I128 = 6  /* signed 128-bit (two's complement) */
 } mp_dtype;
 
 /* Order flag, OR'ed into the dtype argument of any entry point: keys are in
@@ -262,13 +270,14 @@ MP_API int64_t mp_set_capacity(mp_setop op, int64_t na, int64_t nb);
  *   when values are given: any of a_vals, b_vals, out_vals non-NULL) hold
  *   mp_set_capacity(op, na, nb) elements, device, not overlapping an input.
  *   out_count: device pointer to one int64, set to the result length.
- * One partition kernel (Alg. 2 at every tile boundary, Cor. 6) and one
- * kernel that merges each tile, decides each output, and writes the kept
- * ones contiguously (a block scan inside the tile, a decoupled look-back
- * across tiles, so the inputs are read once).  Scratch from the library
- * pool: split points and one status word per tile.  Asynchronous; inputs
- * that are not sorted give an unspecified subsequence and, where a tile's
- * output would pass the capacity, set bit 2 of mp_kernel_error().
+ * Kernels: the partition (Alg. 2 at every tile boundary, Cor. 6); a count
+ * pass that merges each tile and counts the outputs it keeps; a scan of the
+ * counts (in blocks of 1024 tiles); an emit pass that merges each tile
+ * again and writes its kept outputs contiguously at the tile's offset (the
+ * last tile also writes the result length).  Scratch from the library pool:
+ * about 20 bytes per tile of 2048 outputs.  Asynchronous; inputs that are not sorted give an unspecified
+ * subsequence and, where a tile's output would pass the capacity, set bit 2
+ * of mp_kernel_error() (that tile writes nothing).
  */
 MP_API mp_status mp_set_operation(mp_setop op, mp_dtype dtype,
                                   const void* a_keys, const uint32_t* a_vals, int64_t na,
@@ -386,8 +395,8 @@ MP_API mp_status mp_graph_destroy(mp_graph* graph);
  * mp_kernel_error -- SYNCHRONOUS (waits for the device).  Bit flags set by
  * kernels whose bounded waits ran out (1: an mbarrier wait of a TMA-staged
  * merge timed out; the CTA stopped early and its tiles are incomplete;
- * 2: a set operation's tile could not place its output: the look-back over
- * earlier tiles ran out, or the output would pass the capacity).
+ * 2: a set operation's tile output would pass the capacity, which only
+ * unsorted inputs cause; that tile wrote nothing).
  * 0 means no kernel reported a problem since the last reset.  reset != 0
  * clears the flags after reading them.
  */

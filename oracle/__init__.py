@@ -16,6 +16,8 @@ compiles that file with gcc, loads it with ctypes and marshals numpy arrays:
                      of sorted inputs, multiset semantics (merge walk, Sec. I)
 
 Key order: integers natural; float32 numeric with -0.0 before +0.0 (no NaN).
+128-bit keys (``kind="u128"`` or ``"i128"``) are uint64 arrays of shape (n, 2),
+the low word first in each row.
 """
 from __future__ import annotations
 
@@ -63,7 +65,7 @@ def load_library(path: str):
     """ctypes-load an oracle build and declare its functions."""
     lib = ctypes.CDLL(path)
     p, i64 = ctypes.c_void_p, ctypes.c_int64
-    for sfx in _SFX.values():
+    for sfx in list(_SFX.values()) + list(WIDE):
         f = getattr(lib, f"oracle_merge_{sfx}")
         f.argtypes = [p, p, i64, p, p, i64, p, p]
         f.restype = None
@@ -90,7 +92,20 @@ def _load():
     return _lib
 
 
-def _sfx(*arrays):
+WIDE = ("u128", "i128")
+
+
+def _wide(x):
+    """A 128-bit key array as a contiguous (n, 2) uint64 array."""
+    x = np.ascontiguousarray(x, dtype=np.uint64)
+    return x.reshape(-1, 2)
+
+
+def _sfx(*arrays, kind=None):
+    if kind is not None:
+        if kind not in WIDE:
+            raise TypeError(f"unknown key kind {kind}")
+        return kind
     dt = arrays[0].dtype
     for x in arrays[1:]:
         if x.dtype != dt:
@@ -110,41 +125,61 @@ def _c(x, dtype=None):
     return np.ascontiguousarray(x, dtype=dtype)
 
 
-def merge(a, b, av=None, bv=None, lib=None):
+def _keys(x, kind):
+    """(array, count) for a key array of the given kind (None: numpy dtype)."""
+    if kind in WIDE:
+        x = _wide(x)
+        return x, x.shape[0]
+    x = _c(x)
+    return x, x.size
+
+
+def _empty_like_keys(a, n, kind):
+    return np.empty((n, 2), dtype=np.uint64) if kind in WIDE else np.empty(n, dtype=a.dtype)
+
+
+def merge(a, b, av=None, bv=None, lib=None, kind=None):
     """Stable merge of sorted a and b; returns (keys, values or None)."""
-    a, b = _c(a), _c(b)
-    sfx = _sfx(a, b)
+    a, na = _keys(a, kind)
+    b, nb = _keys(b, kind)
+    sfx = _sfx(a, b, kind=kind)
     pairs = av is not None
     if pairs != (bv is not None):
         raise ValueError("give values for both sides or for neither")
     av, bv = _c(av, np.uint32), _c(bv, np.uint32)
-    out = np.empty(a.size + b.size, dtype=a.dtype)
-    outv = np.empty(a.size + b.size, dtype=np.uint32) if pairs else None
-    getattr(lib or _load(), f"oracle_merge_{sfx}")(_ptr(a), _ptr(av), a.size, _ptr(b),
-                                            _ptr(bv), b.size, _ptr(out), _ptr(outv))
+    out = _empty_like_keys(a, na + nb, kind)
+    outv = np.empty(na + nb, dtype=np.uint32) if pairs else None
+    getattr(lib or _load(), f"oracle_merge_{sfx}")(_ptr(a), _ptr(av), na, _ptr(b),
+                                            _ptr(bv), nb, _ptr(out), _ptr(outv))
     return out, outv
 
 
-def split(a, b, diag, lib=None):
+def split(a, b, diag, lib=None, kind=None):
     """Alg. 2: returns (a_start, steps) for cross diagonal ``diag``."""
-    a, b = _c(a), _c(b)
-    sfx = _sfx(a, b)
+    a, na = _keys(a, kind)
+    b, nb = _keys(b, kind)
+    sfx = _sfx(a, b, kind=kind)
     steps = ctypes.c_int64(0)
-    r = getattr(lib or _load(), f"oracle_split_{sfx}")(_ptr(a), a.size, _ptr(b), b.size,
+    r = getattr(lib or _load(), f"oracle_split_{sfx}")(_ptr(a), na, _ptr(b), nb,
                                                 int(diag), ctypes.byref(steps))
     if r == -1:
-        raise ValueError(f"diagonal {diag} outside [0, {a.size + b.size}]")
+        raise ValueError(f"diagonal {diag} outside [0, {na + nb}]")
     if r < 0:
         raise ValueError("diagonal search failed: inputs are not sorted")
     return int(r), int(steps.value)
 
 
-def sort(keys, vals=None, lib=None):
+def sort(keys, vals=None, lib=None, kind=None):
     """Stable bottom-up merge sort; returns sorted copies (keys, values)."""
-    k = np.array(keys, copy=True)
-    sfx = _sfx(k)
+    if kind in WIDE:
+        k = _wide(keys).copy()
+        n = k.shape[0]
+    else:
+        k = np.array(keys, copy=True)
+        n = k.size
+    sfx = _sfx(k, kind=kind)
     v = None if vals is None else np.array(vals, dtype=np.uint32, copy=True)
-    if getattr(lib or _load(), f"oracle_sort_{sfx}")(_ptr(k), _ptr(v), k.size) != 0:
+    if getattr(lib or _load(), f"oracle_sort_{sfx}")(_ptr(k), _ptr(v), n) != 0:
         raise MemoryError("oracle sort: out of host memory")
     return k, v
 
@@ -171,18 +206,19 @@ def merge_batched(a, a_off, b, b_off, av=None, bv=None, lib=None):
 SET_OPS = {"union": 0, "intersection": 1, "difference": 2, "symmetric_difference": 3}
 
 
-def set_op(op, a, b, av=None, bv=None, lib=None):
+def set_op(op, a, b, av=None, bv=None, lib=None, kind=None):
     """Set operation ``op`` (a name in SET_OPS or its code) of sorted a and b,
     multiset semantics; returns (keys, values or None), trimmed to length."""
     code = SET_OPS[op] if isinstance(op, str) else int(op)
-    a, b = _c(a), _c(b)
-    sfx = _sfx(a, b)
+    a, na = _keys(a, kind)
+    b, nb = _keys(b, kind)
+    sfx = _sfx(a, b, kind=kind)
     pairs = av is not None
     if pairs != (bv is not None):
         raise ValueError("give values for both sides or for neither")
     av, bv = _c(av, np.uint32), _c(bv, np.uint32)
-    out = np.empty(a.size + b.size, dtype=a.dtype)
-    outv = np.empty(a.size + b.size, dtype=np.uint32) if pairs else None
-    k = getattr(lib or _load(), f"oracle_set_op_{sfx}")(code, _ptr(a), _ptr(av), a.size, _ptr(b),
-                                                   _ptr(bv), b.size, _ptr(out), _ptr(outv))
+    out = _empty_like_keys(a, na + nb, kind)
+    outv = np.empty(na + nb, dtype=np.uint32) if pairs else None
+    k = getattr(lib or _load(), f"oracle_set_op_{sfx}")(code, _ptr(a), _ptr(av), na, _ptr(b),
+                                                   _ptr(bv), nb, _ptr(out), _ptr(outv))
     return out[:k].copy(), (outv[:k].copy() if pairs else None)

@@ -36,8 +36,10 @@
  *                           last n - m copies.
  *           On duplicate-free inputs these are the ordinary set operations.
  *
- * Key order.  Integers use their natural order.  float32 uses the IEEE-754
- * numeric order with -0.0 ordered before +0.0 (NaN is not a valid input).
+ * Key order.  Integers use their natural order (including the 128-bit
+ * multi-word keys, stored as two 64-bit words, low word first).  float32
+ * uses the IEEE-754 numeric order with -0.0 ordered before +0.0 (NaN is not
+ * a valid input).
  * Values (payloads) are uint32 and move with their keys.
  *
  * Pins: every function here is checked by tests/test_oracle_*.py against a
@@ -57,6 +59,9 @@ static int gt_i32(int32_t x, int32_t y) { return x > y; }
 static int gt_u32(uint32_t x, uint32_t y) { return x > y; }
 static int gt_u64(uint64_t x, uint64_t y) { return x > y; }
 static int gt_i64(int64_t x, int64_t y) { return x > y; }
+/* Multi-word keys: 128-bit integers (two 64-bit words, low word first). */
+static int gt_u128(unsigned __int128 x, unsigned __int128 y) { return x > y; }
+static int gt_i128(__int128 x, __int128 y) { return x > y; }
 /* float32: numeric order, and among equal zeros +0.0 is greater than -0.0. */
 static int gt_f32(float x, float y)
 {
@@ -247,3 +252,5 @@ ORACLE_TYPE(u32, uint32_t)
 ORACLE_TYPE(f32, float)
 ORACLE_TYPE(u64, uint64_t)
 ORACLE_TYPE(i64, int64_t)
+ORACLE_TYPE(u128, unsigned __int128)
+ORACLE_TYPE(i128, __int128)

@@ -180,6 +180,30 @@ def _dtype_code(t: torch.Tensor, descending: bool = False) -> int:
         raise TypeError(f"unsupported key dtype {t.dtype}") from None
 
 
+# 128-bit keys: (n, 2) tensors of 64-bit words, low word first in each row.
+_WIDE = {"u128": 5, "i128": 6}
+MP_U128, MP_I128 = 5, 6
+
+
+def _kcode(t: torch.Tensor, descending: bool = False, wide: str | None = None) -> int:
+    """dtype code of a key tensor; wide="u128"/"i128" for 128-bit keys."""
+    if wide is None:
+        return _dtype_code(t, descending)
+    if wide not in _WIDE:
+        raise TypeError(f"unknown wide key kind {wide!r}")
+    if t.dim() != 2 or t.shape[1] != 2 or t.element_size() != 8:
+        raise TypeError("128-bit keys must be an (n, 2) tensor of 64-bit words")
+    return _WIDE[wide] | (MP_DESCENDING if descending else 0)
+
+
+def _count(t: torch.Tensor, wide: str | None = None) -> int:
+    return t.shape[0] if wide is not None else t.numel()
+
+
+def _new_keys(like: torch.Tensor, n: int, wide: str | None = None) -> torch.Tensor:
+    return torch.empty((n, 2) if wide is not None else n, dtype=like.dtype, device=like.device)
+
+
 def _dev(t: torch.Tensor, what: str) -> int:
     if not t.is_cuda:
         raise ValueError(f"{what} must be a CUDA tensor")
@@ -220,46 +244,47 @@ def mp_last_error() -> str:
 
 
 def mp_merge_keys(a: torch.Tensor, b: torch.Tensor, out: torch.Tensor | None = None,
-                  stream=None, descending: bool = False) -> torch.Tensor:
+                  stream=None, descending: bool = False, wide: str | None = None) -> torch.Tensor:
     """Stable merge of sorted 1-D tensors a and b (ties: a first)."""
     if a.dtype != b.dtype:
         raise TypeError("a and b must have the same dtype")
     if out is None:
-        out = torch.empty(a.numel() + b.numel(), dtype=a.dtype, device=a.device)
-    _check(lib().mp_merge_keys(_dtype_code(a, descending), _dev(a, "a"), a.numel(), _dev(b, "b"), b.numel(),
-                               _dev(out, "out"), _stream(stream)))
+        out = _new_keys(a, _count(a, wide) + _count(b, wide), wide)
+    _check(lib().mp_merge_keys(_kcode(a, descending, wide), _dev(a, "a"), _count(a, wide), _dev(b, "b"),
+                               _count(b, wide), _dev(out, "out"), _stream(stream)))
     return out
 
 
-def mp_merge_pairs(a_keys, a_vals, b_keys, b_vals, out_keys=None, out_vals=None, stream=None, descending: bool = False):
+def mp_merge_pairs(a_keys, a_vals, b_keys, b_vals, out_keys=None, out_vals=None, stream=None,
+                   descending: bool = False, wide: str | None = None):
     """Stable merge moving a uint32 payload with each key."""
     if a_keys.dtype != b_keys.dtype:
         raise TypeError("key dtypes differ")
-    n = a_keys.numel() + b_keys.numel()
+    n = _count(a_keys, wide) + _count(b_keys, wide)
     if out_keys is None:
-        out_keys = torch.empty(n, dtype=a_keys.dtype, device=a_keys.device)
+        out_keys = _new_keys(a_keys, n, wide)
     if out_vals is None:
         out_vals = torch.empty(n, dtype=a_vals.dtype, device=a_keys.device)
-    _check(lib().mp_merge_pairs(_dtype_code(a_keys, descending), _dev(a_keys, "a_keys"), _vals(a_vals, "a_vals"),
-                                a_keys.numel(), _dev(b_keys, "b_keys"), _vals(b_vals, "b_vals"),
-                                b_keys.numel(), _dev(out_keys, "out_keys"), _vals(out_vals, "out_vals"),
+    _check(lib().mp_merge_pairs(_kcode(a_keys, descending, wide), _dev(a_keys, "a_keys"), _vals(a_vals, "a_vals"),
+                                _count(a_keys, wide), _dev(b_keys, "b_keys"), _vals(b_vals, "b_vals"),
+                                _count(b_keys, wide), _dev(out_keys, "out_keys"), _vals(out_vals, "out_vals"),
                                 _stream(stream)))
     return out_keys, out_vals
 
 
 def mp_merge_plan(a_keys, b_keys, a_vals=None, b_vals=None, out_keys=None, out_vals=None,
-                  plan=None, stream=None, descending: bool = False):
+                  plan=None, stream=None, descending: bool = False, wide: str | None = None):
     """Merge with an explicit tile plan (block_threads, items_per_thread[, staging])."""
-    n = a_keys.numel() + b_keys.numel()
+    n = _count(a_keys, wide) + _count(b_keys, wide)
     if out_keys is None:
-        out_keys = torch.empty(n, dtype=a_keys.dtype, device=a_keys.device)
+        out_keys = _new_keys(a_keys, n, wide)
     pairs = a_vals is not None
     if pairs and out_vals is None:
         out_vals = torch.empty(n, dtype=a_vals.dtype, device=a_keys.device)
-    _check(lib().mp_merge_plan(_dtype_code(a_keys, descending), _dev(a_keys, "a_keys"),
-                               _vals(a_vals, "a_vals") if pairs else None, a_keys.numel(),
+    _check(lib().mp_merge_plan(_kcode(a_keys, descending, wide), _dev(a_keys, "a_keys"),
+                               _vals(a_vals, "a_vals") if pairs else None, _count(a_keys, wide),
                                _dev(b_keys, "b_keys"), _vals(b_vals, "b_vals") if pairs else None,
-                               b_keys.numel(), _dev(out_keys, "out_keys"),
+                               _count(b_keys, wide), _dev(out_keys, "out_keys"),
                                _vals(out_vals, "out_vals") if pairs else None, _plan(plan),
                                _stream(stream)))
     return (out_keys, out_vals) if pairs else out_keys
@@ -290,26 +315,27 @@ def mp_set_capacity(op, na: int, nb: int) -> int:
 
 
 def mp_set_operation(op, a_keys, b_keys, a_vals=None, b_vals=None, out_keys=None, out_vals=None,
-                     count=None, stream=None, descending: bool = False, trim: bool = True):
+                     count=None, stream=None, descending: bool = False, trim: bool = True,
+                     wide: str | None = None):
     """Set operation ``op`` ("union", "intersection", "difference",
     "symmetric_difference" or an MP_SET_* code) of sorted a_keys and b_keys
     (multiset semantics).  Returns (keys, values or None, count tensor); with
     trim=True the outputs are sliced to the result length (one device read)."""
     code = _SET_OPS[op] if isinstance(op, str) else int(op)
-    cap = mp_set_capacity(code, a_keys.numel(), b_keys.numel())
+    cap = mp_set_capacity(code, _count(a_keys, wide), _count(b_keys, wide))
     if cap < 0:
         raise MPError(MP_ERR_INVALID_ARG, f"unknown set operation {op!r}")
     if out_keys is None:
-        out_keys = torch.empty(cap, dtype=a_keys.dtype, device=a_keys.device)
+        out_keys = _new_keys(a_keys, cap, wide)
     pairs = a_vals is not None
     if pairs and out_vals is None:
         out_vals = torch.empty(cap, dtype=a_vals.dtype, device=a_keys.device)
     if count is None:
         count = torch.empty(1, dtype=torch.int64, device=a_keys.device)
-    _check(lib().mp_set_operation(code, _dtype_code(a_keys, descending), _dev(a_keys, "a_keys"),
-                                  _vals(a_vals, "a_vals") if pairs else None, a_keys.numel(),
+    _check(lib().mp_set_operation(code, _kcode(a_keys, descending, wide), _dev(a_keys, "a_keys"),
+                                  _vals(a_vals, "a_vals") if pairs else None, _count(a_keys, wide),
                                   _dev(b_keys, "b_keys"), _vals(b_vals, "b_vals") if pairs else None,
-                                  b_keys.numel(), _dev(out_keys, "out_keys"),
+                                  _count(b_keys, wide), _dev(out_keys, "out_keys"),
                                   _vals(out_vals, "out_vals") if pairs else None, _dev(count, "count"),
                                   _stream(stream)))
     if trim:
@@ -325,19 +351,19 @@ def mp_merge_tile_items(dtype, with_values: bool, total: int, plan=None) -> int:
 
 
 def mp_merge_partitioned(a_keys, b_keys, a_split, a_vals=None, b_vals=None, out_keys=None,
-                         out_vals=None, plan=None, stream=None):
+                         out_vals=None, plan=None, stream=None, wide: str | None = None):
     """The merge kernel alone over split points from mp_merge_path_partition
     (spacing = mp_merge_tile_items(...))."""
-    n = a_keys.numel() + b_keys.numel()
+    n = _count(a_keys, wide) + _count(b_keys, wide)
     if out_keys is None:
-        out_keys = torch.empty(n, dtype=a_keys.dtype, device=a_keys.device)
+        out_keys = _new_keys(a_keys, n, wide)
     pairs = a_vals is not None
     if pairs and out_vals is None:
         out_vals = torch.empty(n, dtype=a_vals.dtype, device=a_keys.device)
-    _check(lib().mp_merge_partitioned(_dtype_code(a_keys), _dev(a_keys, "a_keys"),
-                                      _vals(a_vals, "a_vals") if pairs else None, a_keys.numel(),
+    _check(lib().mp_merge_partitioned(_kcode(a_keys, False, wide), _dev(a_keys, "a_keys"),
+                                      _vals(a_vals, "a_vals") if pairs else None, _count(a_keys, wide),
                                       _dev(b_keys, "b_keys"), _vals(b_vals, "b_vals") if pairs else None,
-                                      b_keys.numel(), _dev(out_keys, "out_keys"),
+                                      _count(b_keys, wide), _dev(out_keys, "out_keys"),
                                       _vals(out_vals, "out_vals") if pairs else None,
                                       _dev(a_split, "a_split"), _plan(plan), _stream(stream)))
     return (out_keys, out_vals) if pairs else out_keys
@@ -363,14 +389,15 @@ def mp_merge_pairs_host(a_keys, a_vals, b_keys, b_vals, out_keys, out_vals, stre
     return (out_keys, out_vals) if pairs else out_keys
 
 
-def mp_merge_path_partition(a, b, spacing: int, out=None, stream=None, descending: bool = False):
+def mp_merge_path_partition(a, b, spacing: int, out=None, stream=None, descending: bool = False,
+                            wide: str | None = None):
     """Split points (Alg. 2) at diagonals min(t*spacing, |a|+|b|)."""
-    n = a.numel() + b.numel()
+    n = _count(a, wide) + _count(b, wide)
     nb = (n + spacing - 1) // spacing + 1
     if out is None:
         out = torch.empty(nb, dtype=torch.int64, device=a.device)
-    _check(lib().mp_merge_path_partition(_dtype_code(a, descending), _dev(a, "a"), a.numel(), _dev(b, "b"),
-                                         b.numel(), int(spacing), _dev(out, "a_split"),
+    _check(lib().mp_merge_path_partition(_kcode(a, descending, wide), _dev(a, "a"), _count(a, wide), _dev(b, "b"),
+                                         _count(b, wide), int(spacing), _dev(out, "a_split"),
                                          _stream(stream)))
     return out
 
@@ -380,13 +407,14 @@ def mp_sort_workspace_bytes(dtype, n: int, with_values: bool) -> int:
     return int(lib().mp_sort_workspace_bytes(code, int(n), 1 if with_values else 0))
 
 
-def mp_sort(keys, vals=None, workspace=None, stream=None, descending: bool = False):
+def mp_sort(keys, vals=None, workspace=None, stream=None, descending: bool = False, wide: str | None = None):
     """Stable in-place merge sort of keys (and vals)."""
-    n = keys.numel()
-    need = mp_sort_workspace_bytes(keys.dtype, n, vals is not None)
+    n = _count(keys, wide)
+    code = _kcode(keys, descending, wide)
+    need = mp_sort_workspace_bytes(code & 0xFF, n, vals is not None)
     if workspace is None:
         workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=keys.device)
-    _check(lib().mp_sort(_dtype_code(keys, descending), _dev(keys, "keys"),
+    _check(lib().mp_sort(code, _dev(keys, "keys"),
                          _vals(vals, "vals") if vals is not None else None, n,
                          _dev(workspace, "workspace"), workspace.numel(), _stream(stream)))
     return (keys, vals) if vals is not None else keys
@@ -437,9 +465,9 @@ def mp_merge_grouped(problems, with_values: bool = False, stream=None):
     _check(lib().mp_merge_grouped(arr, n, 1 if with_values else 0, _stream(stream)))
 
 
-def mp_check_sorted(keys, stream=None, descending: bool = False) -> int:
+def mp_check_sorted(keys, stream=None, descending: bool = False, wide: str | None = None) -> int:
     """Synchronous: MP_OK, MP_ERR_NOT_SORTED or MP_ERR_NAN."""
-    return int(lib().mp_check_sorted(_dtype_code(keys, descending), _dev(keys, "keys"), keys.numel(),
+    return int(lib().mp_check_sorted(_kcode(keys, descending, wide), _dev(keys, "keys"), _count(keys, wide),
                                      _stream(stream)))
 
 

@@ -35,9 +35,12 @@ bool key_kind(mp_dtype dtype, KeyKind* k)
     case MP_F32: *k = {4, 0x80000000ull, 0xFFFFFFFFull, 0}; break;
     case MP_U64: *k = {8, 0, 0, 0}; break;
     case MP_I64: *k = {8, 0x8000000000000000ull, 0, 0}; break;
+    // 128-bit keys: flip names the top bit of the top 64-bit word.
+    case MP_U128: *k = {16, 0, 0, 0}; break;
+    case MP_I128: *k = {16, 0x8000000000000000ull, 0, 0}; break;
     default: return false;
     }
-    if (d & MP_DESCENDING) k->inv = k->bytes == 8 ? ~0ull : 0xFFFFFFFFull;
+    if (d & MP_DESCENDING) k->inv = k->bytes == 4 ? 0xFFFFFFFFull : ~0ull;
     return true;
 }
 
@@ -388,7 +391,8 @@ mp_status mp_merge_checksum(mp_dtype dtype, const void* a_keys, const uint32_t* 
                             mp_stream_t stream)
 {
     KeyKind k;
-    if (!key_kind(dtype, &k)) return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_merge_checksum: unknown dtype");
+    if (!key_kind(dtype, &k) || k.bytes == 16)
+        return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_merge_checksum: unknown or 128-bit dtype");
     if (!checksum || ((uintptr_t)checksum & 7)) return fail(MP_ERR_INVALID_ARG, "mp_merge_checksum: checksum must be an aligned device pointer");
     const bool vals = a_vals || b_vals;
     if (na < 0 || nb < 0) return fail(MP_ERR_INVALID_ARG, "mp_merge_checksum: negative size");
@@ -500,9 +504,12 @@ mp_status mp_check_sorted(mp_dtype dtype, const void* keys, int64_t n, mp_stream
                 (const uint32_t*)keys, n,
                 Codec<uint32_t>{(uint32_t)k.flip, (uint32_t)k.fmask, (uint32_t)k.inv},
                 ((int)dtype & 0xFF) == MP_F32, flags);
-        else
+        else if (k.bytes == 8)
             check_sorted_kernel<uint64_t><<<(unsigned)blocks, threads, 0, s>>>(
                 (const uint64_t*)keys, n, Codec<uint64_t>{k.flip, k.fmask, k.inv}, false, flags);
+        else
+            check_sorted_kernel<u128><<<(unsigned)blocks, threads, 0, s>>>(
+                (const u128*)keys, n, make_codec<u128>(k.flip, k.fmask, k.inv), false, flags);
         e = cudaGetLastError();
     }
     unsigned host_flags = 0;

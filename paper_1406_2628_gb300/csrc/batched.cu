@@ -366,7 +366,8 @@ mp_status batched_prepare(mp_dtype dtype, const void* a, const int64_t* a_off, c
                           uint32_t* out_vals, const mp_plan* plan, BatchedProblem* q, Shape* s)
 {
     KeyKind k;
-    if (!key_kind(dtype, &k)) return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_merge_batched: unknown dtype");
+    if (!key_kind(dtype, &k) || k.bytes == 16)
+        return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_merge_batched: unknown or 128-bit dtype");
     if (nseg < 0 || na_total < 0 || nb_total < 0)
         return fail(MP_ERR_INVALID_ARG, "mp_merge_batched: negative size");
     if (nseg == 0 && na_total + nb_total != 0)

@@ -200,7 +200,8 @@ extern "C" mp_status mp_merge_grouped(const mp_merge_desc* descs, int64_t nprob,
     if (nprob == 0) return MP_OK;
     if (nprob > (1 << 30)) return fail(MP_ERR_INVALID_ARG, "mp_merge_grouped: too many problems");
     KeyKind k0;
-    if (!key_kind((mp_dtype)descs[0].dtype, &k0)) return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_merge_grouped: unknown dtype");
+    if (!key_kind((mp_dtype)descs[0].dtype, &k0) || k0.bytes == 16)
+        return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_merge_grouped: unknown or 128-bit dtype");
     const bool vals = with_values != 0;
     std::vector<GroupMergeDesc> h(nprob);
     std::vector<int64_t> first(2 * nprob);
@@ -209,7 +210,8 @@ extern "C" mp_status mp_merge_grouped(const mp_merge_desc* descs, int64_t nprob,
     for (int64_t i = 0; i < nprob; ++i) {
         const mp_merge_desc& d = descs[i];
         KeyKind k;
-        if (!key_kind((mp_dtype)d.dtype, &k)) return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_merge_grouped: unknown dtype");
+        if (!key_kind((mp_dtype)d.dtype, &k) || k.bytes == 16)
+            return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_merge_grouped: unknown or 128-bit dtype");
         if (k.bytes != k0.bytes) return fail(MP_ERR_INVALID_ARG, "mp_merge_grouped: key widths differ");
         mp_status st = check_merge_args_ext(k, d.a_keys, d.a_vals, d.na, d.b_keys, d.b_vals, d.nb,
                                             d.out_keys, d.out_vals, vals, "mp_merge_grouped");

@@ -124,9 +124,7 @@ static TileArgs<K> make_args(const MergeProblem& p, const int64_t* a_split)
     t.run = p.run;
     t.total = p.total();
     t.a_split = a_split;
-    t.codec.flip = (K)p.kind.flip;
-    t.codec.fmask = (K)p.kind.fmask;
-    t.codec.inv = (K)p.kind.inv;
+    t.codec = make_codec<K>(p.kind.flip, p.kind.fmask, p.kind.inv);
     return t;
 }
 
@@ -139,9 +137,12 @@ cudaError_t launch_partition(const MergeProblem& p, int64_t spacing, int64_t* a_
     if (p.kind.bytes == 4)
         partition_kernel<uint32_t><<<(unsigned)blocks, threads, 0, stream>>>(
             make_args<uint32_t>(p, nullptr), spacing, n_bounds, a_split);
-    else
+    else if (p.kind.bytes == 8)
         partition_kernel<uint64_t><<<(unsigned)blocks, threads, 0, stream>>>(
             make_args<uint64_t>(p, nullptr), spacing, n_bounds, a_split);
+    else
+        partition_kernel<u128><<<(unsigned)blocks, threads, 0, stream>>>(
+            make_args<u128>(p, nullptr), spacing, n_bounds, a_split);
     return cudaGetLastError();
 }
 
@@ -253,10 +254,18 @@ static cudaError_t launch_bulk_t(const MergeProblem& p, const int64_t* a_split, 
 #define MP_MERGE_SHAPES(X) X(128, 8) X(256, 8) X(128, 16) X(256, 16) X(512, 8)
 #define MP_BULK_SHAPES(X) X(128, 8) X(256, 8) X(128, 16) X(256, 16)
 #define MP_WARP_SHAPES(X) X(128, 8) X(256, 8) X(128, 16) X(256, 16)
+// 128-bit keys: TMA-staged tiles only.
+#define MP_WIDE_SHAPES(X) X(128, 8) X(256, 8)
 
 bool merge_shape_supported(int key_bytes, bool with_values, const Shape& s)
 {
     (void)with_values;
+    if (key_bytes == 16) {
+#define X(NT_, VT_) if (s.staging == MP_STAGE_BULK && s.nt == NT_ && s.vt == VT_) return true;
+        MP_WIDE_SHAPES(X)
+#undef X
+        return false;
+    }
     if (key_bytes != 4 && key_bytes != 8) return false;
 #define X(NT_, VT_) if (s.nt == NT_ && s.vt == VT_) return true;
     if (s.staging == MP_STAGE_VECTOR) {
@@ -294,7 +303,10 @@ Shape default_merge_shape(int key_bytes, bool with_values, int64_t total)
     // staging registers, so more CTAs stay resident);
     // mp_autotune_merge overrides per size class.
     s.staging = MP_STAGE_BULK;
-    if (key_bytes == 8) {
+    if (key_bytes == 16) {
+        s.nt = 128;
+        s.vt = 8;
+    } else if (key_bytes == 8) {
         s.nt = with_values ? 256 : 128;
         s.vt = with_values ? 8 : 16;
     } else {
@@ -308,6 +320,16 @@ cudaError_t launch_merge_tiles(const MergeProblem& p, const Shape& s, const int6
                                cudaStream_t stream)
 {
     const bool vals = p.vals;
+    if (p.kind.bytes == 16) {
+        if (s.staging != MP_STAGE_BULK) return cudaErrorInvalidValue;
+#define X(NT_, VT_)                                                                            \
+        if (s.nt == NT_ && s.vt == VT_)                                                        \
+            return vals ? launch_bulk_t<u128, true, NT_, VT_>(p, a_split, stream)              \
+                        : launch_bulk_t<u128, false, NT_, VT_>(p, a_split, stream);
+        MP_WIDE_SHAPES(X)
+#undef X
+        return cudaErrorInvalidValue;
+    }
     if (s.staging == MP_STAGE_WARP) {
 #define X(NT_, VT_)                                                                            \
         if (s.nt == NT_ && s.vt == VT_) {                                                      \

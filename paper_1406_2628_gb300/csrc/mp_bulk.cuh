@@ -162,7 +162,7 @@ __device__ __forceinline__ EdgeLoad<E> edge_load(int j, const E* gA, int la, con
         idx = tail0 + (jj - V);
     }
     if (idx >= 0) {
-        e.val = __ldg(g + idx);
+        e.val = ld_global_nc(g + idx);
         e.dst = idx;
     }
     return e;

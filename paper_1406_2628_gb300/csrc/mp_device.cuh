@@ -8,15 +8,26 @@
 // 1...1 0...0 sequence, Prop. 13 puts the path at its transition), so the
 // output splits into equal, independent pieces (Thm 5, Cor. 6, Cor. 7).
 //
-// Everything here works on keys held as unsigned integers (uint32_t or
-// uint64_t bit patterns) and compares them through an order-preserving
-// codec, so one kernel body serves signed, unsigned and float keys.
+// Everything here works on keys held as unsigned integers (uint32_t,
+// uint64_t or 128-bit bit patterns) and compares them through an
+// order-preserving codec, so one kernel body serves signed, unsigned and
+// float keys.
 #pragma once
 
 #include <cstdint>
+#include <cstring>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace mp {
+
+// 128-bit keys (multi-word: two 64-bit words, low word first in memory).
+using u128 = unsigned __int128;
+
+// Signed integer of a key's width (for the sign fill of the codec).
+template <class K>
+using signed_of = typename std::conditional<
+    sizeof(K) == 16, __int128, typename std::conditional<sizeof(K) == 8, int64_t, int32_t>::type>::type;
 
 // ---------------------------------------------------------------------------
 // Key codec.  enc(x) = x ^ ((signfill(x) & fmask) | flip), compared as
@@ -39,9 +50,29 @@ struct Codec {
 template <class K>
 __device__ __forceinline__ K key_enc(K x, Codec<K> c)
 {
-    using S = typename std::conditional<sizeof(K) == 8, int64_t, int32_t>::type;
+    using S = signed_of<K>;
     K fill = (K)((S)x >> (8 * sizeof(K) - 1));
     return x ^ ((fill & c.fmask) | c.flip) ^ c.inv;
+}
+
+// The codec of a key kind given by its top-word masks: flip and fmask act
+// on the key's top 64 bits (for 128-bit keys flip is moved to the top word;
+// fmask, used by float keys only, widens to all bits), inv != 0 complements
+// every bit.
+template <class K>
+__host__ __device__ inline Codec<K> make_codec(uint64_t flip, uint64_t fmask, uint64_t inv)
+{
+    Codec<K> c;
+    if constexpr (sizeof(K) == 16) {
+        c.flip = (K)flip << 64;
+        c.fmask = fmask ? ~(K)0 : (K)0;
+        c.inv = inv ? ~(K)0 : (K)0;
+    } else {
+        c.flip = (K)flip;
+        c.fmask = (K)fmask;
+        c.inv = (K)inv;
+    }
+    return c;
 }
 
 // Codec kinds known at compile time: identity (unsigned keys: the
@@ -64,7 +95,7 @@ __device__ __forceinline__ K key_enc_ck(K x, Codec<K> c)
 template <class K>
 __device__ __forceinline__ K key_dec(K e, Codec<K> c)
 {
-    using S = typename std::conditional<sizeof(K) == 8, int64_t, int32_t>::type;
+    using S = signed_of<K>;
     e ^= c.inv;
     K fill = (K)((S)(~e) >> (8 * sizeof(K) - 1));
     return e ^ ((fill & c.fmask) | c.flip);
@@ -92,7 +123,14 @@ __device__ __forceinline__ void st_global_cs_v4(void* p, uint4 v)
 template <class E>
 __device__ __forceinline__ E ld_global_nc(const E* p)
 {
-    return __ldg(p);
+    if constexpr (sizeof(E) == 16) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+        E e;
+        memcpy(&e, &v, 16);
+        return e;
+    } else {
+        return __ldg(p);
+    }
 }
 
 __device__ __forceinline__ void st_shared_v4(void* p, uint4 v)

@@ -143,10 +143,11 @@ mp_status check_merge_args_ext(const KeyKind& k, const void* a, const uint32_t* 
                                const uint32_t* outv, bool vals, const char* fn, int64_t out_n = -1);
 
 // Merge-based set operations (setops.cu): splits from launch_partition with
-// spacing setop_tile(); status (one word per tile) and counter zeroed.
-int64_t setop_tile();
-cudaError_t launch_setop(const MergeProblem& p, int op, const int64_t* splits, unsigned long long* status,
-                         unsigned int* counter, int64_t cap, int64_t* count, cudaStream_t stream);
+// spacing setop_tile(key bytes); counts (uint32) and offsets (int64): one
+// per tile.
+int64_t setop_tile(int key_bytes);
+cudaError_t launch_setop(const MergeProblem& p, int op, const int64_t* splits, uint32_t* counts,
+                         int64_t* offsets, int64_t cap, int64_t* count, cudaStream_t stream);
 
 // Read-only merge (results folded into a checksum, merge.cu).
 int64_t checksum_tile(int key_bytes, bool vals);

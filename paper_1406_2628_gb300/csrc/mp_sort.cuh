@@ -20,16 +20,23 @@
 namespace mp {
 
 // Padded position of element i of a shared array of E-byte elements.
+// log2 of the elements of size E in 128 bytes (E of 2, 4, 8 or 16 bytes).
+template <class E>
+constexpr int per128_log2()
+{
+    return sizeof(E) == 16 ? 3 : (sizeof(E) == 8 ? 4 : (sizeof(E) == 4 ? 5 : 6));
+}
+
 template <class E>
 __device__ __forceinline__ int padded(int i)
 {
-    return i + (i >> (sizeof(E) == 8 ? 4 : (sizeof(E) == 4 ? 5 : 6)));
+    return i + (i >> per128_log2<E>());
 }
 
 template <class K, bool VALS, int NT, int VT>
 struct SortSmem {
     static constexpr int T = NT * VT;
-    static constexpr int KEYS = T + T / (sizeof(K) == 8 ? 16 : 32) + 1;
+    static constexpr int KEYS = T + (T >> per128_log2<K>()) + 1;
     static constexpr int TAGS = VALS ? T + T / 64 + 2 : 0;
     static constexpr size_t keys_bytes = ((size_t)KEYS * sizeof(K) + 15) / 16 * 16;
     static constexpr size_t tags_bytes = ((size_t)TAGS * 2 + 15) / 16 * 16;

@@ -70,8 +70,8 @@ __device__ __forceinline__ int64_t partition_point(const TileArgs<K>& p, int64_t
     const K* A = q.A;
     const K* B = q.B;
     const Codec<K> c = p.codec;
-    return diagonal_search<K>([&](int64_t i) { return key_enc(__ldg(A + i), c); }, q.na,
-                              [&](int64_t i) { return key_enc(__ldg(B + i), c); }, q.nb,
+    return diagonal_search<K>([&](int64_t i) { return key_enc(ld_global_nc(A + i), c); }, q.na,
+                              [&](int64_t i) { return key_enc(ld_global_nc(B + i), c); }, q.nb,
                               d - q.base);
 }
 

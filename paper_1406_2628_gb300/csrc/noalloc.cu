@@ -64,6 +64,9 @@ extern "C" mp_status mp_merge_noalloc(mp_dtype dtype, const void* a_keys, const 
     if (na >= 0 && nb >= 0 && na + nb > kNoallocMaxTotal)
         return fail(MP_ERR_INVALID_ARG,
                     "mp_merge_noalloc: na + nb exceeds the fixed scratch limit of 1073737728 outputs");
+    const int base = (int)dtype & 0xFF;
+    if (base == MP_U128 || base == MP_I128)
+        return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_merge_noalloc: 128-bit keys are not supported");
     MergeProblem p;
     Shape s;
     const bool vals = a_vals || b_vals || out_vals;

@@ -536,7 +536,8 @@ mp_status mp_queue_submit(mp_queue* q, const mp_request* r, uint64_t* ticket)
 {
     if (!q || !r || !ticket) return fail(MP_ERR_INVALID_ARG, "mp_queue_submit: NULL argument");
     KeyKind k;
-    if (!key_kind((mp_dtype)r->dtype, &k)) return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_queue_submit: unknown dtype");
+    if (!key_kind((mp_dtype)r->dtype, &k) || k.bytes == 16)
+        return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_queue_submit: unknown or 128-bit dtype");
     if (r->op != MP_OP_MERGE && r->op != MP_OP_SORT) return fail(MP_ERR_INVALID_ARG, "mp_queue_submit: unknown op");
     if (r->source != MP_SRC_HOST && r->source != MP_SRC_DEVICE && r->source != MP_SRC_GENERATE)
         return fail(MP_ERR_INVALID_ARG, "mp_queue_submit: unknown source");

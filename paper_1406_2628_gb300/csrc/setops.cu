@@ -18,12 +18,13 @@
 //      edge is completed with three galloping searches in global memory per
 //      tile (the run ending at a0-1 in A, at b0-1 in B, the run starting at
 //      b1 in B), done while the copies are in flight;
-//   3. count-then-scatter in one pass: a block scan of the kept counts gives
-//      each output its place in the tile, a decoupled look-back over the
-//      tiles' published counts gives the tile's place in the result, and the
-//      kept outputs are gathered and written contiguously.
-// Tiles take their index from an atomic counter, so every tile a CTA looks
-// back on is already held by a running CTA; the look-back waits are bounded.
+//   3. count-then-scatter: a count kernel walks every tile and stores the
+//      number of outputs it keeps; a one-CTA scan turns the counts into
+//      tile offsets (and the result length); an emit kernel walks every tile
+//      again, places each kept output by a block scan of the kept counts and
+//      writes them contiguously at the tile's offset.  The inputs are read
+//      twice, but no CTA ever waits on another (a single-pass version with a
+//      decoupled look-back across tiles spent most of its time in that wait).
 #include <algorithm>
 
 #include "mp_bulk.cuh"
@@ -33,36 +34,24 @@
 
 namespace mp {
 
-// Bit set in the kernel error word when a set operation's look-back gave up
-// or its output would pass the capacity (inputs not sorted).
+// Bit set in the kernel error word when a set operation's output would pass
+// the capacity (inputs not sorted).
 #define MP_KERR_SETOP 2u
 
 template <class K>
 struct SetArgs {
-    TileArgs<K> t;               // the merge problem (run == 0) and split points
-    int op;                      // MP_SET_*
+    TileArgs<K> t;           // the merge problem (run == 0) and split points
+    int op;                  // MP_SET_*
     int64_t ntiles;
-    int64_t cap;                 // output capacity (elements)
-    unsigned long long* status;  // per tile: flag (top 2 bits) | count
-    unsigned int* tile_counter;  // [0]: next tile, [1]: abort flag of this launch
-    int64_t* count;              // result length (device)
+    int64_t cap;             // output capacity (elements)
+    uint32_t* counts;           // count kernel: kept outputs per tile
+    const int64_t* offsets;     // emit kernel: exclusive prefix inside the scan block
+    const int64_t* block_sums;  // emit kernel: total of each scan block
+    int64_t* count;             // emit kernel (last tile): the result length
 };
 
-constexpr unsigned long long ST_AGG = 1ull << 62;   // tile count published
-constexpr unsigned long long ST_PRE = 2ull << 62;   // inclusive prefix published
-constexpr unsigned long long ST_VAL = (1ull << 62) - 1;
-
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
-{
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v)
-{
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
+// Tiles per block of the offset scan.
+constexpr int SET_SCAN_BLOCK = 1024;
 
 // First index of the run of X[i]'s key that contains i (galloping down).
 template <class K>
@@ -141,217 +130,313 @@ __device__ __forceinline__ int first_equal(const K* s, int lo, int hi, K v)
     return hi;
 }
 
+// Decision for an output whose key v also occurs on the other side and
+// repeats (or may repeat) beyond the immediate neighbours: measure the runs.
+//   from A (window index ai, B pointer bi = start of v's run in B): keep for
+//     intersection iff r_a < n, for difference / symmetric iff r_a >= n,
+//     where r_a = rank of this copy in A's run of v and n = length of v's
+//     run in B;
+//   from B (index bi, A pointer ai = one past v's run in A): keep for union /
+//     symmetric iff r_b >= m, r_b = rank in B's run, m = length of A's run.
+template <class K>
+__device__ __noinline__ bool setop_slow(bool from_a, K v, int ai, int bi, const K* sA, int la, const K* sB,
+                                        int lb, int op, const SetCtx<K>& x, int64_t a0, int64_t b0)
+{
+    if (from_a) {
+        int64_t r_a = 0;
+        if ((ai > 0 && sA[ai - 1] == v) || (ai == 0 && x.has_prev_a && x.prev_a == v)) {
+            const int f = first_equal(sA, 0, ai, v);
+            const int64_t start = (f == 0 && x.has_prev_a && x.prev_a == v) ? x.lb_prev_a : a0 + f;
+            r_a = a0 + ai - start;
+        }
+        int64_t end;
+        if (bi >= lb) {
+            end = x.ub_next_b;
+        } else {
+            int lo = bi, hi = lb;  // sB[lo] == v; first index != v in (lo, lb]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (sB[mid] == v) lo = mid;
+                else hi = mid;
+            }
+            end = (hi == lb && x.has_next_b && x.next_b == v) ? x.ub_next_b : b0 + hi;
+        }
+        const int64_t n = end - (b0 + bi);
+        return op == MP_SET_INTERSECTION ? r_a < n : r_a >= n;
+    }
+    int64_t start;
+    if (ai == 0) {
+        start = x.lb_prev_a;
+    } else {
+        const int f = first_equal(sA, 0, ai - 1, v);
+        start = (f == 0 && x.has_prev_a && x.prev_a == v) ? x.lb_prev_a : a0 + f;
+    }
+    const int64_t m = a0 + ai - start;
+    int64_t r_b = 0;
+    if ((bi > 0 && sB[bi - 1] == v) || (bi == 0 && x.has_prev_b && x.prev_b == v)) {
+        const int f = first_equal(sB, 0, bi, v);
+        const int64_t bs = (f == 0 && x.has_prev_b && x.prev_b == v) ? x.lb_prev_b : b0 + f;
+        r_b = b0 + bi - bs;
+    }
+    return r_b >= m;
+}
+
 // Walk VT outputs of the tile's merge from split (ai, bi) and decide each:
-// records sources (A: 0..la-1, B: la..) and a bit mask of kept outputs.
-template <class K, int VT, int CK>
+// records sources (A: 0..la-1, B: la..; when SRC) and returns a bit mask of
+// kept outputs.  Equal keys are equal bits.  The walk is the plain merge
+// (Alg. 1's Merge) recording three bits per output: taken from A; its key
+// is held by the other side (for an A output: B's pointer is at an equal
+// key, ties taking A; for a B output: the last A taken is equal); its key
+// repeats on its own side (the previous element of that side is equal).
+// An output whose key is not repeated is the first copy of its run (rank
+// 0), and rank 0 < n, rank 0 >= m hold or fail whatever the run lengths
+// n, m >= 1 of the other side are, so the operation's rule reduces to bit
+// operations:
+//   union         A outputs, and B outputs without a partner;
+//   intersection  A outputs with a partner;
+//   difference    A outputs without a partner;
+//   symmetric     outputs without a partner.
+// Outputs that have a partner and repeat go to setop_slow (rare).
+template <class K, int VT, int CK, bool SRC>
 __device__ __forceinline__ uint32_t setop_walk(const K* sA, int la, const K* sB, int lb, int ai, int bi,
                                                int n_valid, int op, const SetCtx<K>& x, int64_t a0,
                                                int64_t b0, Codec<K> c, uint32_t (&packed)[VT / 2])
 {
-    const bool keep_a_alone = op != MP_SET_INTERSECTION;
-    const bool keep_b_alone = op == MP_SET_UNION || op == MP_SET_SYMMETRIC_DIFFERENCE;
+    static_assert(VT <= 32, "one bit per output");
+    const int ai0 = ai, bi0 = bi;
     K ra = sA[ai], rb = sB[bi];
     K ka = key_enc_ck<CK>(ra, c), kb = key_enc_ck<CK>(rb, c);
     bool last_a_ok = ai > 0 || x.has_prev_a;
     K last_a = ai > 0 ? sA[ai - 1] : x.prev_a;
     bool last_b_ok = bi > 0 || x.has_prev_b;
     K last_b = bi > 0 ? sB[bi - 1] : x.prev_b;
-    uint32_t keep = 0;
+    uint32_t took_a = 0, partner = 0, repeat = 0;
 #pragma unroll
     for (int i = 0; i < VT; ++i) {
         const bool take_a = (bi >= lb) || (ai < la && !(ka > kb));
-        bool kp = false;
-        if (take_a) {
-            const K v = ra;
-            if (i < n_valid) {
-                // The B pointer is where v's run in B starts (ties take A).
-                const bool match_b = bi < lb ? rb == v : (x.has_next_b && x.next_b == v);
-                if (!match_b || op == MP_SET_UNION) {
-                    kp = keep_a_alone;
-                } else {
-                    // Rank of this copy in A's run of v.
-                    int64_t r_a = 0;
-                    if (last_a_ok && last_a == v) {
-                        const int f = first_equal(sA, 0, ai, v);
-                        const int64_t start = (f == 0 && x.has_prev_a && x.prev_a == v) ? x.lb_prev_a : a0 + f;
-                        r_a = a0 + ai - start;
-                    }
-                    // Length of v's run in B (from b0 + bi).
-                    int64_t end;
-                    if (bi >= lb) {
-                        end = x.ub_next_b;
-                    } else if (bi + 1 < lb && sB[bi + 1] != v) {
-                        end = b0 + bi + 1;
-                    } else {
-                        int lo = bi, hi = lb;  // sB[lo] == v; first index != v in (lo, lb]
-                        while (hi - lo > 1) {
-                            const int mid = (lo + hi) >> 1;
-                            if (sB[mid] == v) lo = mid;
-                            else hi = mid;
-                        }
-                        end = (hi == lb && x.has_next_b && x.next_b == v) ? x.ub_next_b : b0 + hi;
-                    }
-                    const int64_t n = end - (b0 + bi);
-                    kp = op == MP_SET_INTERSECTION ? r_a < n : r_a >= n;
-                }
-            }
-            const uint32_t src = (uint32_t)ai;
+        const K v = take_a ? ra : rb;
+        const bool a_last = last_a_ok && last_a == v;
+        const bool match = take_a ? (bi < lb ? rb == v : (x.has_next_b && x.next_b == v)) : a_last;
+        const bool dup = take_a ? a_last : (last_b_ok && last_b == v);
+        took_a |= (uint32_t)take_a << i;
+        partner |= (uint32_t)match << i;
+        repeat |= (uint32_t)dup << i;
+        if constexpr (SRC) {
+            const uint32_t src = take_a ? (uint32_t)ai : (uint32_t)(la + bi);
             if (i & 1) packed[i / 2] |= src << 16;
             else packed[i / 2] = src;
+        }
+        const K* nxt = take_a ? (sA + (ai < la ? ai + 1 : la)) : (sB + bi + 1);
+        const K rn = *nxt;
+        const K kn = key_enc_ck<CK>(rn, c);
+        if (take_a) {
             last_a = v;
             last_a_ok = true;
+            ra = rn;
+            ka = kn;
             ++ai;
-            ra = sA[ai < la ? ai : la];
-            ka = key_enc_ck<CK>(ra, c);
         } else {
-            const K v = rb;
-            if (i < n_valid && keep_b_alone) {
-                // The A pointer is one past v's run in A.
-                const bool match_a = last_a_ok && last_a == v;
-                if (!match_a) {
-                    kp = true;
-                } else {
-                    int64_t start;
-                    if (ai == 0) {
-                        start = x.lb_prev_a;
-                    } else if (ai >= 2 && sA[ai - 2] != v) {
-                        start = a0 + ai - 1;
-                    } else {
-                        const int f = first_equal(sA, 0, ai - 1, v);
-                        start = (f == 0 && x.has_prev_a && x.prev_a == v) ? x.lb_prev_a : a0 + f;
-                    }
-                    const int64_t m = a0 + ai - start;
-                    int64_t r_b = 0;
-                    if (last_b_ok && last_b == v) {
-                        const int f = first_equal(sB, 0, bi, v);
-                        const int64_t bs = (f == 0 && x.has_prev_b && x.prev_b == v) ? x.lb_prev_b : b0 + f;
-                        r_b = b0 + bi - bs;
-                    }
-                    kp = r_b >= m;
-                }
-            }
-            const uint32_t src = (uint32_t)(la + bi);
-            if (i & 1) packed[i / 2] |= src << 16;
-            else packed[i / 2] = src;
             last_b = v;
             last_b_ok = true;
+            rb = rn;
+            kb = kn;
             ++bi;
-            rb = sB[bi];
-            kb = key_enc_ck<CK>(rb, c);
         }
-        if (kp) keep |= 1u << i;
     }
-    return keep;
+    const uint32_t all = VT == 32 ? 0xFFFFFFFFu : ((1u << VT) - 1);
+    const uint32_t valid = n_valid >= VT ? all : (n_valid > 0 ? (1u << n_valid) - 1 : 0u);
+    uint32_t keep, slow_sides;
+    switch (op) {
+    case MP_SET_UNION:
+        keep = took_a | ~partner;
+        slow_sides = ~took_a;
+        break;
+    case MP_SET_INTERSECTION:
+        keep = took_a & partner;
+        slow_sides = took_a;
+        break;
+    case MP_SET_DIFFERENCE:
+        keep = took_a & ~partner;
+        slow_sides = took_a;
+        break;
+    default:
+        keep = ~partner;
+        slow_sides = all;
+        break;
+    }
+    uint32_t slow = partner & repeat & slow_sides & valid;
+    while (slow) {
+        const int i = __ffs(slow) - 1;
+        slow &= slow - 1;
+        const int na = __popc(took_a & ((1u << i) - 1));
+        const bool take_a = (took_a >> i) & 1;
+        const int ai_i = ai0 + na, bi_i = bi0 + (i - na);
+        const K v = take_a ? sA[ai_i] : sB[bi_i];
+        const bool kp = setop_slow(take_a, v, ai_i, bi_i, sA, la, sB, lb, op, x, a0, b0);
+        keep = (keep & ~(1u << i)) | ((uint32_t)kp << i);
+    }
+    return keep & valid;
 }
 
-// Exclusive prefix of this tile's count over all earlier tiles (warp 0).
-// Returns false if a wait ran out.
-__device__ __forceinline__ bool look_back(unsigned long long* status, int64_t tile, unsigned long long count,
-                                          const unsigned int* abort_flag, unsigned long long* excl_out)
-{
-    constexpr uint32_t SPIN_LIMIT = 1u << 20;
-    const int lane = threadIdx.x & 31;
-    if (tile == 0) {
-        if (lane == 0) st_release_u64(&status[0], ST_PRE | count);
-        *excl_out = 0;
-        return true;
-    }
-    if (lane == 0) st_release_u64(&status[tile], ST_AGG | count);
-    unsigned long long excl = 0;
-    int64_t q = tile - 1;
-    bool ok = true;
-    while (true) {
-        const int64_t idx = q - lane;
-        unsigned long long w = ST_PRE;  // before tile 0: a zero prefix
-        if (idx >= 0) {
-            w = ld_acquire_u64(&status[idx]);
-            uint32_t spins = 0;
-            while ((w >> 62) == 0) {
-                // Give up after the limit, or early once a CTA of this
-                // launch has failed (a failed tile never publishes).
-                if (++spins > SPIN_LIMIT || (spins % 1024 == 0 && *(volatile const unsigned int*)abort_flag != 0))
-                    break;
-                __nanosleep(64);
-                w = ld_acquire_u64(&status[idx]);
-            }
-        }
-        if (__any_sync(0xFFFFFFFFu, (w >> 62) == 0)) {
-            ok = false;
-            break;
-        }
-        const unsigned pre = __ballot_sync(0xFFFFFFFFu, (w >> 62) == 2);
-        const int first = pre ? __ffs(pre) - 1 : 31;  // nearest published prefix
-        unsigned long long v = lane <= first ? (w & ST_VAL) : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-        excl += v;
-        if (pre) break;
-        q -= 32;
-    }
-    if (ok && lane == 0) st_release_u64(&status[tile], ST_PRE | (excl + count));
-    *excl_out = excl;
-    return ok;
-}
-
-template <class K, bool VALS, int NT, int VT, int CK>
-__global__ void __launch_bounds__(NT, 2) setop_kernel(SetArgs<K> p, unsigned int* err)
+// Stage tile `tile`, find the runs crossing the window edges, and walk this
+// thread's VT outputs.  Returns false (all threads) if the staging wait ran
+// out.
+template <class K, bool VALS, int NT, int VT, int CK, bool SRC>
+__device__ __forceinline__ bool setop_tile_walk(const SetArgs<K>& p, int64_t tile, unsigned char* smem,
+                                                unsigned int* err, TilePlace<K>& t,
+                                                TileView<K, VALS, NT, VT>& v, uint32_t (&packed)[VT / 2],
+                                                uint32_t& keep, unsigned long long* place = nullptr)
 {
     using SM = SetSmem<K, VALS, NT, VT>;
     constexpr int T = NT * VT;
-    constexpr int NW = NT / 32;
-    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const BulkLayout<K, VALS, NT, VT> lay(smem);
     SetCtx<K>& x = *reinterpret_cast<SetCtx<K>*>(smem + SM::ctx_off);
-    unsigned long long* scan = reinterpret_cast<unsigned long long*>(smem + SM::scan_off);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    if (tid == 0) scan[NW + 2] = atomicAdd(p.tile_counter, 1u);
-    bulk_init(lay.bar);
-    __syncthreads();
-    const int64_t tile = (int64_t)scan[NW + 2];
-    if (tile >= p.ntiles) return;  // uniform
-
     const TileArgs<K>& ta = p.t;
-    const TilePlace<K> t = tile_place(ta, tile, T, ta.a_split);
-    const auto v = stage_view<K, VALS, NT, VT>(t, lay.sk, lay.sv, lay.sidx);
+    t = tile_place(ta, tile, T, ta.a_split);
+    v = stage_view<K, VALS, NT, VT>(t, lay.sk, lay.sv, lay.sidx);
     const int64_t a0 = t.gA - ta.a, b0 = t.gB - ta.b;
     const int64_t b1 = b0 + t.lb;
-    if (warp == 3) {  // edge runs, in global memory, while the copies fly
+    bulk_init(lay.bar);
+    __syncthreads();
+    if (place && warp == 2) {
+        // The tile's place in the result: its offset inside its scan block
+        // plus the totals of the earlier blocks (while the copies fly).
+        const int64_t blk = tile / SET_SCAN_BLOCK;
+        unsigned long long sum = 0;
+        for (int64_t j = lane; j < blk; j += 32) sum += (unsigned long long)p.block_sums[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+        if (lane == 0) *place = sum + (unsigned long long)p.offsets[tile];
+    }
+    if (warp == 3) {  // the keys just outside the windows, while the copies fly
         if (lane == 0) {
             x.has_prev_a = a0 > 0;
-            if (a0 > 0) {
-                x.prev_a = ta.a[a0 - 1];
-                x.lb_prev_a = run_start(ta.a, a0 - 1);
-            }
+            if (a0 > 0) x.prev_a = ld_global_nc(ta.a + a0 - 1);
         } else if (lane == 1) {
             x.has_prev_b = b0 > 0;
-            if (b0 > 0) {
-                x.prev_b = ta.b[b0 - 1];
-                x.lb_prev_b = run_start(ta.b, b0 - 1);
-            }
+            if (b0 > 0) x.prev_b = ld_global_nc(ta.b + b0 - 1);
         } else if (lane == 2) {
             x.has_next_b = b1 < ta.nb;
-            if (b1 < ta.nb) {
-                x.next_b = ta.b[b1];
-                x.ub_next_b = run_end(ta.b, ta.nb, b1);
-            }
+            if (b1 < ta.nb) x.next_b = ld_global_nc(ta.b + b1);
         }
     }
-    if (!bulk_stage<K, VALS, NT, VT>(t, v, lay.bar, 0, err)) {  // (the barrier also publishes x)
-        if (tid == 0) atomicExch(p.tile_counter + 1, 1u);
-        return;
+    // The staging barrier also publishes x.
+    if (!bulk_stage<K, VALS, NT, VT>(t, v, lay.bar, 0, err)) return false;
+    // Run lengths are consulted only for outputs whose key repeats on its own
+    // side and occurs on the other (setop_slow).  A run crossing a window
+    // edge is then measured in global memory, once per tile (the condition
+    // is the same on every thread): the run ending at a0-1 in A when A's
+    // window starts inside it, or when B's window starts with its key and
+    // that key repeats in B; the run ending at b0-1 in B when B's window
+    // starts inside it; the run starting at b1 in B when B's window ends
+    // inside it, or when A's window ends with its key and that key repeats
+    // in A.  Duplicate-free inputs never need them.
+    const int la = t.la, lb = t.lb;
+    const bool b0_rep = lb > 0 && ((lb > 1 && v.sB[1] == v.sB[0]) || (x.has_prev_b && x.prev_b == v.sB[0]));
+    const bool a_end_rep =
+        la > 0 && ((la > 1 && v.sA[la - 2] == v.sA[la - 1]) || (la == 1 && x.has_prev_a && x.prev_a == v.sA[0]));
+    const bool need_a = x.has_prev_a && ((la > 0 && v.sA[0] == x.prev_a) || (b0_rep && v.sB[0] == x.prev_a));
+    const bool need_b = x.has_prev_b && lb > 0 && v.sB[0] == x.prev_b;
+    const bool need_n = x.has_next_b &&
+                        ((lb > 0 && v.sB[lb - 1] == x.next_b) || (a_end_rep && v.sA[la - 1] == x.next_b));
+    if (need_a || need_b || need_n) {
+        if (warp == 3) {
+            if (lane == 0 && need_a) x.lb_prev_a = run_start(ta.a, a0 - 1);
+            if (lane == 1 && need_b) x.lb_prev_b = run_start(ta.b, b0 - 1);
+            if (lane == 2 && need_n) x.ub_next_b = run_end(ta.b, ta.nb, b1);
+        }
+        __syncthreads();
     }
-
-    // Merge walk with decisions.
     const int L = t.la + t.lb;
     const int diag = tid * VT < L ? tid * VT : L;
     const int ai = smem_diagonal_search_ck<CK>(v.sA, t.la, v.sB, t.lb, diag, ta.codec);
-    uint32_t packed[VT / 2];
-    const uint32_t keep = setop_walk<K, VT, CK>(v.sA, t.la, v.sB, t.lb, ai, diag - ai, L - diag, p.op, x, a0,
-                                                b0, ta.codec, packed);
+    keep = setop_walk<K, VT, CK, SRC>(v.sA, t.la, v.sB, t.lb, ai, diag - ai, L - diag, p.op, x, a0, b0,
+                                      ta.codec, packed);
+    return true;
+}
 
-    // Block scan of the kept counts.
+// Pass 1: kept outputs per tile.
+template <class K, bool VALS, int NT, int VT, int CK>
+__global__ void __launch_bounds__(NT, sizeof(K) == 4 ? 4 : 2) setop_count_kernel(SetArgs<K> p, unsigned int* err)
+{
+    using SM = SetSmem<K, VALS, NT, VT>;
+    constexpr int NW = NT / 32;
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long* scan = reinterpret_cast<unsigned long long*>(smem + SM::scan_off);
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    TilePlace<K> t;
+    TileView<K, VALS, NT, VT> v;
+    uint32_t packed[VT / 2];
+    uint32_t keep = 0;
+    if (!setop_tile_walk<K, VALS, NT, VT, CK, false>(p, blockIdx.x, smem, err, t, v, packed, keep, nullptr))
+        return;
+    int c = __popc(keep);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+    if (lane == 0) scan[warp] = (unsigned long long)c;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long total = 0;
+        for (int w = 0; w < NW; ++w) total += scan[w];
+        p.counts[blockIdx.x] = (uint32_t)total;
+    }
+}
+
+// Pass 2: exclusive scan of the counts inside blocks of NT tiles:
+// offsets[t] = counts of the earlier tiles of t's block, block_sums[b] = the
+// block's total.  The emit kernel adds the block sums of earlier blocks.
+template <int NT>
+__global__ void __launch_bounds__(NT) setop_scan_kernel(const uint32_t* counts, int64_t ntiles,
+                                                        int64_t* offsets, int64_t* block_sums)
+{
+    __shared__ unsigned long long wsum[NT / 32];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t i = (int64_t)blockIdx.x * NT + tid;
+    const unsigned long long c = i < ntiles ? counts[i] : 0;
+    unsigned long long incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned long long w = lane < NT / 32 ? wsum[lane] : 0;
+        unsigned long long wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < NT / 32) wsum[lane] = wi - w;
+        if (lane == 31) block_sums[blockIdx.x] = (int64_t)wi;
+    }
+    __syncthreads();
+    if (i < ntiles) offsets[i] = (int64_t)(wsum[warp] + incl - c);
+}
+
+// Pass 3: walk again, place the kept outputs, write them at the tile's offset.
+template <class K, bool VALS, int NT, int VT, int CK>
+__global__ void __launch_bounds__(NT, sizeof(K) == 4 ? 4 : 2) setop_emit_kernel(SetArgs<K> p, unsigned int* err)
+{
+    using SM = SetSmem<K, VALS, NT, VT>;
+    constexpr int NW = NT / 32;
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long* scan = reinterpret_cast<unsigned long long*>(smem + SM::scan_off);
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    TilePlace<K> t;
+    TileView<K, VALS, NT, VT> v;
+    uint32_t packed[VT / 2];
+    uint32_t keep = 0;
+    if (!setop_tile_walk<K, VALS, NT, VT, CK, true>(p, blockIdx.x, smem, err, t, v, packed, keep, &scan[NW + 1]))
+        return;
     const int c = __popc(keep);
     int incl = c;
 #pragma unroll
@@ -362,74 +447,87 @@ __global__ void __launch_bounds__(NT, 2) setop_kernel(SetArgs<K> p, unsigned int
     if (lane == 31) scan[warp] = (unsigned long long)incl;
     __syncthreads();
     if (warp == 0) {
-        unsigned long long w = lane < NW ? scan[lane] : 0;
+        const unsigned long long w = lane < NW ? scan[lane] : 0;
         unsigned long long wi = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
             if (lane >= o) wi += y;
         }
-        const unsigned long long total = __shfl_sync(0xFFFFFFFFu, wi, 31);
-        unsigned long long g = 0;
-        const bool ok = look_back(p.status, tile, total, p.tile_counter + 1, &g);
         if (lane < NW) scan[lane] = wi - w;  // exclusive warp offsets
-        if (lane == 0) {
-            scan[NW] = total;
-            scan[NW + 1] = ok ? g : ~0ull;
-        }
+        if (lane == 31) scan[NW] = wi;       // tile total
     }
     __syncthreads();
-    const unsigned long long total = scan[NW];
-    const unsigned long long g = scan[NW + 1];
-    if (g == ~0ull || g + total > (unsigned long long)p.cap) {
-        if (tid == 0) {
-            atomicOr(err, MP_KERR_SETOP);
-            atomicExch(p.tile_counter + 1, 1u);
-        }
+    const int64_t g = (int64_t)scan[NW + 1];
+    const int n_out = (int)scan[NW];
+    if (g < 0 || g + n_out > p.cap) {
+        if (tid == 0) atomicOr(err, MP_KERR_SETOP);
         return;
     }
-    // Compact the kept sources into the index array (positions in the tile's
-    // share of the result).
+    // Compact the kept sources into the index array (the staged windows stay
+    // where they are; only indices move).
+    uint16_t* sidx = v.sidx;
     int pos = (int)scan[warp] + incl - c;
 #pragma unroll
     for (int i = 0; i < VT; ++i) {
-        if (keep & (1u << i)) lay.sidx[pos++] = (uint16_t)((packed[i / 2] >> (16 * (i & 1))) & 0xFFFF);
+        if (keep & (1u << i)) sidx[pos++] = (uint16_t)((packed[i / 2] >> (16 * (i & 1))) & 0xFFFF);
     }
     __syncthreads();
-    const int n_out = (int)total;
+    const TileArgs<K>& ta = p.t;
     K* gout = ta.out + g;
     for (int j = tid; j < n_out; j += NT) {
-        const int s = lay.sidx[j];
+        const int s = sidx[j];
         gout[j] = s < t.la ? v.sA[s] : v.sB[s - t.la];
     }
     if constexpr (VALS) {
         uint32_t* gvout = ta.outv + g;
         for (int j = tid; j < n_out; j += NT) {
-            const int s = lay.sidx[j];
+            const int s = sidx[j];
             gvout[j] = s < t.la ? v.vA[s] : v.vB[s - t.la];
         }
     }
-    if (tile == p.ntiles - 1 && tid == 0) *p.count = (int64_t)(g + total);
+    if (tid == 0 && blockIdx.x == p.ntiles - 1) *p.count = g + n_out;
 }
 
 // ---------------------------------------------------------------------------
 // Host side.
 // ---------------------------------------------------------------------------
 constexpr int SET_NT = 256;
-constexpr int SET_VT = 8;
+// Items per thread: 4096-output tiles for 4-byte keys, 2048 otherwise.
+constexpr int set_vt(int key_bytes) { return key_bytes == 4 ? 16 : 8; }
 
-int64_t setop_tile() { return (int64_t)SET_NT * SET_VT; }
+int64_t setop_tile(int key_bytes) { return (int64_t)SET_NT * set_vt(key_bytes); }
+
+static cudaError_t pdl_launch_cfg(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, unsigned grid,
+                                  unsigned block, size_t smem, cudaStream_t stream)
+{
+    cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaSuccess;
+}
 
 template <class K, bool VALS, int CK>
-static cudaError_t launch_setop_ck(const MergeProblem& mp_, int op, const int64_t* splits,
-                                   unsigned long long* status, unsigned int* counter, int64_t cap,
-                                   int64_t* count, cudaStream_t stream)
+static cudaError_t launch_setop_ck(const MergeProblem& mp_, int op, const int64_t* splits, uint32_t* counts,
+                                   int64_t* offsets, int64_t* block_sums, int64_t cap, int64_t* count,
+                                   cudaStream_t stream)
 {
-    using SM = SetSmem<K, VALS, SET_NT, SET_VT>;
-    auto kern = setop_kernel<K, VALS, SET_NT, SET_VT, CK>;
+    constexpr int VT = set_vt((int)sizeof(K));
+    using SM = SetSmem<K, VALS, SET_NT, VT>;
+    using SMK = SetSmem<K, false, SET_NT, VT>;  // the count pass stages keys only
+    auto kcount = setop_count_kernel<K, false, SET_NT, VT, CK>;
+    auto kemit = setop_emit_kernel<K, VALS, SET_NT, VT, CK>;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
+        cudaError_t e = cudaFuncSetAttribute(kcount, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMK::bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kemit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
         if (e != cudaSuccess) return e;
         configured = true;
     }
@@ -448,46 +546,56 @@ static cudaError_t launch_setop_ck(const MergeProblem& mp_, int op, const int64_
     t.run = 0;
     t.total = mp_.na + mp_.nb;
     t.a_split = splits;
-    t.codec.flip = (K)mp_.kind.flip;
-    t.codec.fmask = (K)mp_.kind.fmask;
-    t.codec.inv = (K)mp_.kind.inv;
+    t.codec = make_codec<K>(mp_.kind.flip, mp_.kind.fmask, mp_.kind.inv);
     a.op = op;
-    a.ntiles = ceil_div(t.total, setop_tile());
+    a.ntiles = ceil_div(t.total, setop_tile((int)sizeof(K)));
     a.cap = cap;
-    a.status = status;
-    a.tile_counter = counter;
+    a.counts = counts;
+    a.offsets = offsets;
+    a.block_sums = block_sums;
     a.count = count;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)a.ntiles);
-    cfg.blockDim = dim3(SET_NT);
-    cfg.dynamicSmemBytes = SM::bytes;
-    cfg.stream = stream;
+    cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, a, err);
+    // The count pass reads keys only: same arguments, no values.
+    SetArgs<K> ak = a;
+    ak.t.av = ak.t.bv = nullptr;
+    ak.t.outv = nullptr;
+    pdl_launch_cfg(cfg, attr, (unsigned)a.ntiles, SET_NT, SMK::bytes, stream);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kcount, ak, err);
+    if (e != cudaSuccess) return e;
+    const int64_t nblk = ceil_div(a.ntiles, (int64_t)SET_SCAN_BLOCK);
+    pdl_launch_cfg(cfg, attr, (unsigned)nblk, SET_SCAN_BLOCK, 0, stream);
+    e = cudaLaunchKernelEx(&cfg, setop_scan_kernel<SET_SCAN_BLOCK>, (const uint32_t*)counts, a.ntiles, offsets,
+                           block_sums);
+    if (e != cudaSuccess) return e;
+    pdl_launch_cfg(cfg, attr, (unsigned)a.ntiles, SET_NT, SM::bytes, stream);
+    return cudaLaunchKernelEx(&cfg, kemit, a, err);
 }
 
 template <class K, bool VALS>
-static cudaError_t launch_setop_t(const MergeProblem& p, int op, const int64_t* splits,
-                                  unsigned long long* status, unsigned int* counter, int64_t cap, int64_t* count,
-                                  cudaStream_t stream)
+static cudaError_t launch_setop_t(const MergeProblem& p, int op, const int64_t* splits, uint32_t* counts,
+                                  int64_t* offsets, int64_t cap, int64_t* count, cudaStream_t stream)
 {
+    // Block sums follow the offsets (one per SET_SCAN_BLOCK tiles).
+    const int64_t ntiles = ceil_div(p.na + p.nb, setop_tile(p.kind.bytes));
+    int64_t* block_sums = offsets + ntiles;
     if (p.kind.identity())
-        return launch_setop_ck<K, VALS, CODEC_IDENTITY>(p, op, splits, status, counter, cap, count, stream);
-    return launch_setop_ck<K, VALS, CODEC_RUNTIME>(p, op, splits, status, counter, cap, count, stream);
+        return launch_setop_ck<K, VALS, CODEC_IDENTITY>(p, op, splits, counts, offsets, block_sums, cap, count,
+                                                        stream);
+    return launch_setop_ck<K, VALS, CODEC_RUNTIME>(p, op, splits, counts, offsets, block_sums, cap, count, stream);
 }
 
-cudaError_t launch_setop(const MergeProblem& p, int op, const int64_t* splits, unsigned long long* status,
-                         unsigned int* counter, int64_t cap, int64_t* count, cudaStream_t stream)
+cudaError_t launch_setop(const MergeProblem& p, int op, const int64_t* splits, uint32_t* counts,
+                         int64_t* offsets, int64_t cap, int64_t* count, cudaStream_t stream)
 {
     if (p.kind.bytes == 4)
-        return p.vals ? launch_setop_t<uint32_t, true>(p, op, splits, status, counter, cap, count, stream)
-                      : launch_setop_t<uint32_t, false>(p, op, splits, status, counter, cap, count, stream);
-    return p.vals ? launch_setop_t<uint64_t, true>(p, op, splits, status, counter, cap, count, stream)
-                  : launch_setop_t<uint64_t, false>(p, op, splits, status, counter, cap, count, stream);
+        return p.vals ? launch_setop_t<uint32_t, true>(p, op, splits, counts, offsets, cap, count, stream)
+                      : launch_setop_t<uint32_t, false>(p, op, splits, counts, offsets, cap, count, stream);
+    if (p.kind.bytes == 16)
+        return p.vals ? launch_setop_t<u128, true>(p, op, splits, counts, offsets, cap, count, stream)
+                      : launch_setop_t<u128, false>(p, op, splits, counts, offsets, cap, count, stream);
+    return p.vals ? launch_setop_t<uint64_t, true>(p, op, splits, counts, offsets, cap, count, stream)
+                  : launch_setop_t<uint64_t, false>(p, op, splits, counts, offsets, cap, count, stream);
 }
 
 }  // namespace mp
@@ -539,19 +647,19 @@ mp_status mp_set_operation(mp_setop op, mp_dtype dtype, const void* a_keys, cons
     p.na = na;
     p.nb = nb;
     p.run = 0;
-    const int64_t T = setop_tile();
+    const int64_t T = setop_tile(k.bytes);
     const int64_t ntiles = ceil_div(na + nb, T);
     const size_t split_bytes = (size_t)(ntiles + 1) * 8;
-    const size_t status_bytes = (size_t)ntiles * 8;
+    const size_t offset_bytes = (size_t)(ntiles + ceil_div(ntiles, (int64_t)SET_SCAN_BLOCK)) * 8;
+    const size_t count_bytes = (size_t)ntiles * 4;
     unsigned char* scratch = nullptr;
-    st = scratch_alloc((void**)&scratch, split_bytes + status_bytes + 16, s);
+    st = scratch_alloc((void**)&scratch, split_bytes + offset_bytes + count_bytes, s);
     if (st != MP_OK) return st;
     int64_t* splits = reinterpret_cast<int64_t*>(scratch);
-    unsigned long long* status = reinterpret_cast<unsigned long long*>(scratch + split_bytes);
-    unsigned int* counter = reinterpret_cast<unsigned int*>(scratch + split_bytes + status_bytes);
-    cudaError_t e = cudaMemsetAsync(status, 0, status_bytes + 16, s);
-    if (e == cudaSuccess) e = launch_partition(p, T, splits, s);
-    if (e == cudaSuccess) e = launch_setop(p, (int)op, splits, status, counter, cap, out_count, s);
+    int64_t* offsets = reinterpret_cast<int64_t*>(scratch + split_bytes);
+    uint32_t* counts = reinterpret_cast<uint32_t*>(scratch + split_bytes + offset_bytes);
+    cudaError_t e = launch_partition(p, T, splits, s);
+    if (e == cudaSuccess) e = launch_setop(p, (int)op, splits, counts, offsets, cap, out_count, s);
     scratch_free(scratch, s);
     return e == cudaSuccess ? MP_OK : cuda_fail(e, fn);
 }

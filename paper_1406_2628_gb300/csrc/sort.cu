@@ -28,15 +28,19 @@ __global__ void __launch_bounds__(NT) block_sort_kernel(const K* in, const uint3
 static constexpr int BS_NT = 256;
 static constexpr int BS_VT4 = 16;  // 4-byte keys: tile 4096
 static constexpr int BS_VT8 = 8;   // 8-byte keys: tile 2048
+static constexpr int BS_VT16 = 4;  // 16-byte keys: tile 1024
 
-static int64_t block_tile(int key_bytes) { return (int64_t)BS_NT * (key_bytes == 8 ? BS_VT8 : BS_VT4); }
+static int64_t block_tile(int key_bytes)
+{
+    return (int64_t)BS_NT * (key_bytes == 16 ? BS_VT16 : (key_bytes == 8 ? BS_VT8 : BS_VT4));
+}
 
 static Shape sort_merge_shape(int key_bytes)
 {
     // Tile of the merge passes; must divide 2 * block tile.
     Shape s;
-    s.nt = 256;
-    s.vt = key_bytes == 8 ? 8 : 16;
+    s.nt = key_bytes == 16 ? 128 : 256;
+    s.vt = key_bytes == 4 ? 16 : 8;
     s.staging = MP_STAGE_BULK;
     return s;
 }
@@ -71,10 +75,7 @@ static cudaError_t launch_block_sort(const K* in, const uint32_t* vin, K* out, u
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    Codec<K> c;
-    c.flip = (K)kind.flip;
-    c.fmask = (K)kind.fmask;
-    c.inv = (K)kind.inv;
+    const Codec<K> c = make_codec<K>(kind.flip, kind.fmask, kind.inv);
     const int64_t blocks = ceil_div(n, (int64_t)NT * VT);
     kern<<<(unsigned)blocks, NT, SM::bytes, stream>>>(in, vin, out, vout, n, c);
     return cudaGetLastError();
@@ -89,6 +90,13 @@ static cudaError_t block_sort(const KeyKind& kind, const void* in, const uint32_
                 (const uint32_t*)in, vin, (uint32_t*)out, vout, n, kind, stream);
         return launch_block_sort<uint32_t, false, BS_NT, BS_VT4>(
             (const uint32_t*)in, nullptr, (uint32_t*)out, nullptr, n, kind, stream);
+    }
+    if (kind.bytes == 16) {
+        if (vin)
+            return launch_block_sort<u128, true, BS_NT, BS_VT16>((const u128*)in, vin, (u128*)out, vout, n, kind,
+                                                                 stream);
+        return launch_block_sort<u128, false, BS_NT, BS_VT16>((const u128*)in, nullptr, (u128*)out, nullptr, n,
+                                                              kind, stream);
     }
     if (vin)
         return launch_block_sort<uint64_t, true, BS_NT, BS_VT8>(

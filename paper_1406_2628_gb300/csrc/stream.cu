@@ -110,7 +110,7 @@ __device__ __forceinline__ void ring_edge(const Ring<E>& r, uint32_t f0, uint32_
     uint32_t h, t;
     ring_interior(r, f0, f1, h, t);
     const uint32_t idx = j < V ? f0 + j : t + (j - V);
-    if (j < V ? idx < h : idx < f1) r.s[slot_of<C>(idx, r.ph)] = __ldg(r.g + idx);
+    if (j < V ? idx < h : idx < f1) r.s[slot_of<C>(idx, r.ph)] = ld_global_nc(r.g + idx);
 }
 
 // Alg. 2 in global memory, one warp: the number of A elements among the
@@ -137,7 +137,7 @@ __device__ __forceinline__ int64_t warp_split(const K* A, int64_t na, const K* B
             valid = true;
         }
         bool pred = true;
-        if (valid) pred = key_enc_ck<CK>(__ldg(A + m), c) > key_enc_ck<CK>(__ldg(B + (d - 1 - m)), c);
+        if (valid) pred = key_enc_ck<CK>(ld_global_nc(A + m), c) > key_enc_ck<CK>(ld_global_nc(B + (d - 1 - m)), c);
         const unsigned ball = __ballot_sync(0xFFFFFFFFu, pred);
         const int f = ball ? __ffs(ball) - 1 : 32;
         const int64_t m_first = __shfl_sync(0xFFFFFFFFu, m, f & 31);
@@ -429,9 +429,7 @@ static cudaError_t launch_stream_ck(const MergeProblem& p, cudaStream_t stream)
     a.nb = p.nb;
     a.total = total;
     a.steps_per_cta = steps;
-    a.codec.flip = (K)p.kind.flip;
-    a.codec.fmask = (K)p.kind.fmask;
-    a.codec.inv = (K)p.kind.inv;
+    a.codec = make_codec<K>(p.kind.flip, p.kind.fmask, p.kind.inv);
     kern<<<(unsigned)grid, NT, SM::bytes, stream>>>(a, err);
     return cudaGetLastError();
 }
@@ -474,7 +472,7 @@ int64_t stream_auto_limit(int key_bytes, bool with_values)
 
 Shape stream_default_shape(int key_bytes, bool with_values)
 {
-    if (key_bytes == 8 && with_values) return Shape{128, 8, MP_STAGE_STREAM};
+    if (key_bytes == 16 || (key_bytes == 8 && with_values)) return Shape{128, 8, MP_STAGE_STREAM};
     return Shape{256, 8, MP_STAGE_STREAM};
 }
 
@@ -488,6 +486,9 @@ cudaError_t launch_merge_stream(const MergeProblem& p, const Shape& s, cudaStrea
         if (p.kind.bytes == 4)                                                                   \
             return vals ? launch_stream_t<uint32_t, true, NT_, VT_, L_>(p, stream)               \
                         : launch_stream_t<uint32_t, false, NT_, VT_, L_>(p, stream);             \
+        if (p.kind.bytes == 16)                                                                  \
+            return vals ? launch_stream_t<u128, true, NT_, VT_, L_>(p, stream)                   \
+                        : launch_stream_t<u128, false, NT_, VT_, L_>(p, stream);                 \
         return vals ? launch_stream_t<uint64_t, true, NT_, VT_, L_>(p, stream)                   \
                     : launch_stream_t<uint64_t, false, NT_, VT_, L_>(p, stream);                 \
     }

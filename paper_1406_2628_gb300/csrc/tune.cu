@@ -120,6 +120,9 @@ mp_status mp_autotune_merge(mp_dtype dtype, const void* a_keys, const uint32_t* 
     std::vector<Shape> cands = merge_shapes();
     for (const Shape& c : stream_shapes()) cands.push_back(c);
     for (const Shape& cand : cands) {
+        const bool ok = cand.staging == MP_STAGE_STREAM ? stream_shape_supported(cand)
+                                                        : merge_shape_supported(k.bytes, vals, cand);
+        if (!ok) continue;
         mp_plan p{cand.nt, cand.vt, cand.staging, 0};
         // Warm-up (also sets kernel attributes), then the fastest of reps.
         st = mp_merge_plan(dtype, a_keys, a_vals, na, b_keys, b_vals, nb, out_keys, out_vals, &p, stream);

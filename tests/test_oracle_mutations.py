@@ -13,6 +13,7 @@ import pytest
 import oracle
 import test_oracle_pins as pins
 import test_oracle_setops as setpins
+import test_oracle_wide as widepins
 
 # (name, text in mp_oracle.c, replacement)
 MUTATIONS = [
@@ -58,6 +59,12 @@ MUTATIONS = [
         }                                                                            \\
     }                                                                                \\
     for (; i < na; i++)"""),
+    ("128-bit keys compared on the low word only",
+     "static int gt_u128(unsigned __int128 x, unsigned __int128 y) { return x > y; }",
+     "static int gt_u128(unsigned __int128 x, unsigned __int128 y) { return (uint64_t)x > (uint64_t)y; }"),
+    ("signed 128-bit keys compared without their sign",
+     "static int gt_i128(__int128 x, __int128 y) { return x > y; }",
+     "static int gt_i128(__int128 x, __int128 y) { return (unsigned __int128)x > (unsigned __int128)y; }"),
     ("set op: difference keeps B's leftovers",
      "const int keep_b_alone = (op == 0 || op == 3);",
      "const int keep_b_alone = (op == 0 || op == 2 || op == 3);"),
@@ -74,6 +81,8 @@ PINS = [
     setpins.test_set_ops_hand_example,
     setpins.test_set_ops_cardinality_identities,
     setpins.test_set_ops_exhaustive_tiny_vs_counting,
+    lambda: widepins.test_wide_merge_split_exhaustive_tiny("u128"),
+    lambda: widepins.test_wide_merge_split_exhaustive_tiny("i128"),
 ]
 PINS_DTYPE = [
     pins.test_closed_form_all_equal,
