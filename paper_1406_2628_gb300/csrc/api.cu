@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 #include <string>
 
 #include "mp_device.cuh"
@@ -255,6 +256,202 @@ __global__ void check_sorted_kernel(const K* x, int64_t n, Codec<K> c, bool is_f
     if (f) atomicOr(flags, f);
 }
 
+// ---------------------------------------------------------------------------
+// End-to-end merge of host arrays, pipelined.  The inputs cross to the device
+// in C chunks (A[x_{i-1}, x_i] and B[y_{i-1}, y_i], each with one element of
+// overlap).  Once chunk i has landed, the prefix A[0, x_i) ∪ B[0, y_i) fixes
+// the merged output up to
+//   d_i = min(x_i + #{B[0, y_i) < A[x_i]},  y_i + #{A[0, x_i) <= B[y_i]})
+// (the positions at which A[x_i] and B[y_i] would be emitted, ties taking A;
+// a missing element counts as +inf), with a(d_i) = x_i when the first term
+// is the smaller and d_i - y_i otherwise.  A one-thread cut kernel computes
+// (d_i, a(d_i)); the outputs [d_{i-1}, d_i) are merged (Alg. 1 on that piece,
+// Cor. 6) and copied back while later inputs are still arriving, so the
+// input and output copies overlap.
+// ---------------------------------------------------------------------------
+template <class K>
+__device__ int64_t count_less(const K* X, int64_t n, K v, Codec<K> c, bool or_equal)
+{
+    const K kv = key_enc(v, c);
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const K km = key_enc(X[mid], c);
+        if (or_equal ? !(km > kv) : (km < kv))
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+template <class K>
+__global__ void host_cut_kernel(const K* A, int64_t na, int64_t x, const K* B, int64_t nb, int64_t y, Codec<K> c,
+                                int64_t* cut)
+{
+    constexpr int64_t INF = INT64_MAX;
+    const int64_t ra = x < na ? x + count_less(B, y, A[x], c, false) : INF;
+    const int64_t rb = y < nb ? y + count_less(A, x, B[y], c, true) : INF;
+    if (ra == INF && rb == INF) {
+        cut[0] = na + nb;
+        cut[1] = na;
+    } else if (ra <= rb) {
+        cut[0] = ra;
+        cut[1] = x;
+    } else {
+        cut[0] = rb;
+        cut[1] = rb - y;
+    }
+}
+
+static cudaError_t launch_host_cut(const KeyKind& k, const void* A, int64_t na, int64_t x, const void* B,
+                                   int64_t nb, int64_t y, int64_t* cut, cudaStream_t s)
+{
+    if (k.bytes == 4)
+        host_cut_kernel<uint32_t><<<1, 1, 0, s>>>((const uint32_t*)A, na, x, (const uint32_t*)B, nb, y,
+                                                  make_codec<uint32_t>(k.flip, k.fmask, k.inv), cut);
+    else if (k.bytes == 8)
+        host_cut_kernel<uint64_t><<<1, 1, 0, s>>>((const uint64_t*)A, na, x, (const uint64_t*)B, nb, y,
+                                                  make_codec<uint64_t>(k.flip, k.fmask, k.inv), cut);
+    else
+        host_cut_kernel<u128><<<1, 1, 0, s>>>((const u128*)A, na, x, (const u128*)B, nb, y,
+                                              make_codec<u128>(k.flip, k.fmask, k.inv), cut);
+    return cudaGetLastError();
+}
+
+static mp_status host_merge_pipelined(mp_dtype dtype, const KeyKind& k, const void* a_keys,
+                                      const uint32_t* a_vals, int64_t na, const void* b_keys,
+                                      const uint32_t* b_vals, int64_t nb, void* out_keys, uint32_t* out_vals,
+                                      bool vals, cudaStream_t s)
+{
+    static const char* fn = "mp_merge_pairs_host";
+    const int64_t n = na + nb;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t kb = (size_t)k.bytes;
+    const size_t row = kb + (vals ? 4 : 0);
+    // Chunks of at least 64 MB of input (at most 32); small merges take one.
+    const int nchunk = (int)std::min<int64_t>(32, std::max<int64_t>(1, (int64_t)((size_t)n * row >> 26)));
+    const size_t off_b = al(na * kb), off_o = off_b + al(nb * kb), off_av = off_o + al(n * kb);
+    const size_t off_bv = off_av + (vals ? al(na * 4) : 0), off_ov = off_bv + (vals ? al(nb * 4) : 0);
+    const size_t off_cut = off_ov + (vals ? al(n * 4) : 0);
+    const size_t total = off_cut + al((size_t)nchunk * 16);
+    char* d = nullptr;
+    mp_status st = scratch_alloc((void**)&d, total, s);
+    if (st != MP_OK) return st;
+    char* dA = d;
+    char* dB = d + off_b;
+    char* dO = d + off_o;
+    uint32_t* dAV = vals ? (uint32_t*)(d + off_av) : nullptr;
+    uint32_t* dBV = vals ? (uint32_t*)(d + off_bv) : nullptr;
+    uint32_t* dOV = vals ? (uint32_t*)(d + off_ov) : nullptr;
+    int64_t* dcut = (int64_t*)(d + off_cut);
+
+    cudaStream_t s_in = nullptr, s_cut = nullptr, s_out = nullptr;
+    std::vector<cudaEvent_t> ev_in(nchunk, nullptr), ev_cut(nchunk, nullptr), ev_merged(nchunk, nullptr);
+    cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s_cut, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s_out, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming);
+    for (int i = 0; i < nchunk && e == cudaSuccess; ++i) {
+        e = cudaEventCreateWithFlags(&ev_in[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_cut[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_merged[i], cudaEventDisableTiming);
+    }
+    // Everything starts after the scratch allocation on the caller's stream.
+    if (e == cudaSuccess) e = cudaEventRecord(ev_start, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_in, ev_start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, ev_start, 0);
+
+    // Input chunk i: A[x_{i-1}, min(x_i + 1, na)), B likewise (the extra
+    // element is the next chunk's first, needed by the cut).
+    auto xa = [&](int i) { return i < 0 ? (int64_t)0 : (i == nchunk - 1 ? na : (int64_t)((double)na * (i + 1) / nchunk)); };
+    auto yb = [&](int i) { return i < 0 ? (int64_t)0 : (i == nchunk - 1 ? nb : (int64_t)((double)nb * (i + 1) / nchunk)); };
+    auto copy_in = [&](const void* src, char* dst, size_t esz, int64_t lo, int64_t hi) -> cudaError_t {
+        if (hi <= lo) return cudaSuccess;
+        return cudaMemcpyAsync(dst + lo * esz, (const char*)src + lo * esz, (size_t)(hi - lo) * esz,
+                               cudaMemcpyHostToDevice, s_in);
+    };
+    // Per-thread pinned landing place for the cuts (read by the host).
+    static thread_local int64_t* h_cut = nullptr;
+    if (e == cudaSuccess && !h_cut) e = cudaHostAlloc((void**)&h_cut, 32 * 16, cudaHostAllocDefault);
+    int64_t a_copied = 0, b_copied = 0;  // every element is copied once
+    for (int i = 0; i < nchunk && e == cudaSuccess; ++i) {
+        const int64_t a_lo = a_copied, a_hi = std::max(a_copied, std::min(xa(i) + 1, na));
+        const int64_t b_lo = b_copied, b_hi = std::max(b_copied, std::min(yb(i) + 1, nb));
+        a_copied = a_hi;
+        b_copied = b_hi;
+        e = copy_in(a_keys, dA, kb, a_lo, a_hi);
+        if (e == cudaSuccess) e = copy_in(b_keys, dB, kb, b_lo, b_hi);
+        if (vals && e == cudaSuccess) e = copy_in(a_vals, (char*)dAV, 4, a_lo, a_hi);
+        if (vals && e == cudaSuccess) e = copy_in(b_vals, (char*)dBV, 4, b_lo, b_hi);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_in[i], s_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_cut, ev_in[i], 0);
+        if (e == cudaSuccess) e = launch_host_cut(k, dA, na, xa(i), dB, nb, yb(i), dcut + 2 * i, s_cut);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_cut + 2 * i, dcut + 2 * i, 16, cudaMemcpyDeviceToHost, s_cut);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_cut[i], s_cut);
+    }
+    // Merge and copy out each settled piece of the output as soon as its cut
+    // is known (the host reads each cut; the copies keep running meanwhile).
+    int64_t d_prev = 0, a_prev = 0;
+    for (int i = 0; i < nchunk && e == cudaSuccess && st == MP_OK; ++i) {
+        e = cudaEventSynchronize(ev_cut[i]);
+        if (e != cudaSuccess) break;
+        const int64_t d_i = h_cut[2 * i], a_i = h_cut[2 * i + 1];
+        if (d_i < d_prev || a_i < a_prev || d_i > n || a_i > na || d_i - a_i > nb) {
+            st = fail(MP_ERR_INTERNAL, "mp_merge_pairs_host: inconsistent chunk cut (inputs not sorted?)");
+            break;
+        }
+        if (d_i > d_prev) {
+            const int64_t b_prev = d_prev - a_prev, b_i = d_i - a_i;
+            e = cudaStreamWaitEvent(s, ev_cut[i], 0);
+            if (e != cudaSuccess) break;
+            st = merge_impl(dtype, dA + a_prev * kb, vals ? dAV + a_prev : nullptr, a_i - a_prev,
+                            dB + b_prev * kb, vals ? dBV + b_prev : nullptr, b_i - b_prev, dO + d_prev * kb,
+                            vals ? dOV + d_prev : nullptr, vals, nullptr, s, fn);
+            if (st != MP_OK) break;
+            e = cudaEventRecord(ev_merged[i], s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, ev_merged[i], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync((char*)out_keys + d_prev * kb, dO + d_prev * kb, (size_t)(d_i - d_prev) * kb,
+                                    cudaMemcpyDeviceToHost, s_out);
+            if (vals && e == cudaSuccess)
+                e = cudaMemcpyAsync(out_vals + d_prev, dOV + d_prev, (size_t)(d_i - d_prev) * 4,
+                                    cudaMemcpyDeviceToHost, s_out);
+        }
+        d_prev = d_i;
+        a_prev = a_i;
+    }
+    if (e == cudaSuccess && st == MP_OK && d_prev != n)
+        st = fail(MP_ERR_INTERNAL, "mp_merge_pairs_host: chunks did not cover the output");
+    // The scratch is freed on the caller's stream after every copy and cut.
+    cudaError_t e2 = cudaEventRecord(ev_done, s_out);
+    if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, ev_done, 0);
+    if (e2 == cudaSuccess) e2 = cudaEventRecord(ev_done, s_cut);
+    if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, ev_done, 0);
+    if (e2 == cudaSuccess) e2 = cudaEventRecord(ev_done, s_in);
+    if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, ev_done, 0);
+    scratch_free(d, s);
+    const cudaError_t e3 = cudaStreamSynchronize(s);
+    for (int i = 0; i < nchunk; ++i) {
+        if (ev_in[i]) cudaEventDestroy(ev_in[i]);
+        if (ev_cut[i]) cudaEventDestroy(ev_cut[i]);
+        if (ev_merged[i]) cudaEventDestroy(ev_merged[i]);
+    }
+    if (ev_start) cudaEventDestroy(ev_start);
+    if (ev_done) cudaEventDestroy(ev_done);
+    if (s_in) cudaStreamDestroy(s_in);
+    if (s_cut) cudaStreamDestroy(s_cut);
+    if (s_out) cudaStreamDestroy(s_out);
+    if (st != MP_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, fn);
+    if (e2 != cudaSuccess) return cuda_fail(e2, fn);
+    if (e3 != cudaSuccess) return cuda_fail(e3, fn);
+    return MP_OK;
+}
+
 }  // namespace mp
 
 using namespace mp;
@@ -351,39 +548,8 @@ mp_status mp_merge_pairs_host(mp_dtype dtype, const void* a_keys, const uint32_t
                                     vals, "mp_merge_pairs_host");
     if (st != MP_OK) return st;
     if (na + nb == 0) return MP_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    const int64_t n = na + nb;
-    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t kb = (size_t)k.bytes;
-    const size_t off_b = al(na * kb), off_o = off_b + al(nb * kb), off_av = off_o + al(n * kb);
-    const size_t off_bv = off_av + (vals ? al(na * 4) : 0), off_ov = off_bv + (vals ? al(nb * 4) : 0);
-    const size_t total = off_ov + (vals ? al(n * 4) : 0);
-    char* d = nullptr;
-    st = scratch_alloc((void**)&d, total, s);
-    if (st != MP_OK) return st;
-    cudaError_t e = cudaSuccess;
-    if (na) e = cudaMemcpyAsync(d, a_keys, na * kb, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && nb) e = cudaMemcpyAsync(d + off_b, b_keys, nb * kb, cudaMemcpyHostToDevice, s);
-    if (vals) {
-        if (e == cudaSuccess && na) e = cudaMemcpyAsync(d + off_av, a_vals, na * 4, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess && nb) e = cudaMemcpyAsync(d + off_bv, b_vals, nb * 4, cudaMemcpyHostToDevice, s);
-    }
-    if (e != cudaSuccess) {
-        scratch_free(d, s);
-        return cuda_fail(e, "mp_merge_pairs_host: copy in");
-    }
-    st = merge_impl(dtype, d, vals ? (const uint32_t*)(d + off_av) : nullptr, na, d + off_b,
-                    vals ? (const uint32_t*)(d + off_bv) : nullptr, nb, d + off_o,
-                    vals ? (uint32_t*)(d + off_ov) : nullptr, vals, nullptr, s, "mp_merge_pairs_host");
-    if (st == MP_OK) {
-        e = cudaMemcpyAsync(out_keys, d + off_o, n * kb, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess && vals) e = cudaMemcpyAsync(out_vals, d + off_ov, n * 4, cudaMemcpyDeviceToHost, s);
-    }
-    scratch_free(d, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (st != MP_OK) return st;
-    if (e != cudaSuccess) return cuda_fail(e, "mp_merge_pairs_host");
-    return MP_OK;
+    return host_merge_pipelined(dtype, k, a_keys, a_vals, na, b_keys, b_vals, nb, out_keys, out_vals, vals,
+                                (cudaStream_t)stream);
 }
 
 mp_status mp_merge_checksum(mp_dtype dtype, const void* a_keys, const uint32_t* a_vals, int64_t na,
