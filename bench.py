@@ -49,6 +49,7 @@ PEAK_FALLBACK_GBS = 6800.0
 KERNEL_SOURCES = ["paper_1406_2628_gb300/csrc/merge.cu", "paper_1406_2628_gb300/csrc/mp_tile.cuh",
                   "paper_1406_2628_gb300/csrc/mp_device.cuh", "paper_1406_2628_gb300/csrc/mp_bulk.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "merge_tile_kernel_large_kv_traffic.json")
+SORT_BLOCK_4B = 8192  # keys per block-sort tile for 4-byte keys (the first of the sort's HBM passes)
 
 
 def parse_args():
@@ -445,7 +446,7 @@ def extra_sort(mp, torch, dev, n=1 << 28, reps=3):
                 if r:
                     times.append(e0.elapsed_time(e1))
             ms = min(times)
-            blocks = (n + 4095) // 4096
+            blocks = (n + SORT_BLOCK_4B - 1) // SORT_BLOCK_4B
             passes = 1 + max(0, math.ceil(math.log2(blocks)))
             res[f"{dtype}_{order}"] = {"ms": ms, "gkeys_s": n / ms / 1e6,
                                        "eff_gbs": passes * 2 * n * 4 / ms / 1e6, "hbm_passes": passes}

@@ -302,6 +302,7 @@ __global__ void host_cut_kernel(const K* A, int64_t na, int64_t x, const K* B, i
         cut[0] = rb;
         cut[1] = rb - y;
     }
+    __threadfence_system();  // cut may be host memory the host reads after the kernel
 }
 
 static cudaError_t launch_host_cut(const KeyKind& k, const void* A, int64_t na, int64_t x, const void* B,
@@ -333,8 +334,7 @@ static mp_status host_merge_pipelined(mp_dtype dtype, const KeyKind& k, const vo
     const int nchunk = (int)std::min<int64_t>(32, std::max<int64_t>(1, (int64_t)((size_t)n * row >> 26)));
     const size_t off_b = al(na * kb), off_o = off_b + al(nb * kb), off_av = off_o + al(n * kb);
     const size_t off_bv = off_av + (vals ? al(na * 4) : 0), off_ov = off_bv + (vals ? al(nb * 4) : 0);
-    const size_t off_cut = off_ov + (vals ? al(n * 4) : 0);
-    const size_t total = off_cut + al((size_t)nchunk * 16);
+    const size_t total = off_ov + (vals ? al(n * 4) : 0);
     char* d = nullptr;
     mp_status st = scratch_alloc((void**)&d, total, s);
     if (st != MP_OK) return st;
@@ -344,7 +344,6 @@ static mp_status host_merge_pipelined(mp_dtype dtype, const KeyKind& k, const vo
     uint32_t* dAV = vals ? (uint32_t*)(d + off_av) : nullptr;
     uint32_t* dBV = vals ? (uint32_t*)(d + off_bv) : nullptr;
     uint32_t* dOV = vals ? (uint32_t*)(d + off_ov) : nullptr;
-    int64_t* dcut = (int64_t*)(d + off_cut);
 
     cudaStream_t s_in = nullptr, s_cut = nullptr, s_out = nullptr;
     std::vector<cudaEvent_t> ev_in(nchunk, nullptr), ev_cut(nchunk, nullptr), ev_merged(nchunk, nullptr);
@@ -373,9 +372,15 @@ static mp_status host_merge_pipelined(mp_dtype dtype, const KeyKind& k, const vo
         return cudaMemcpyAsync(dst + lo * esz, (const char*)src + lo * esz, (size_t)(hi - lo) * esz,
                                cudaMemcpyHostToDevice, s_in);
     };
-    // Per-thread pinned landing place for the cuts (read by the host).
+    // Per-thread landing place for the cuts: pinned host memory that the cut
+    // kernel writes directly (mapped), so no cut waits behind a bulk copy on
+    // the copy engines.
     static thread_local int64_t* h_cut = nullptr;
-    if (e == cudaSuccess && !h_cut) e = cudaHostAlloc((void**)&h_cut, 32 * 16, cudaHostAllocDefault);
+    static thread_local int64_t* h_cut_dev = nullptr;
+    if (e == cudaSuccess && !h_cut) {
+        e = cudaHostAlloc((void**)&h_cut, 32 * 16, cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&h_cut_dev, h_cut, 0);
+    }
     int64_t a_copied = 0, b_copied = 0;  // every element is copied once
     for (int i = 0; i < nchunk && e == cudaSuccess; ++i) {
         const int64_t a_lo = a_copied, a_hi = std::max(a_copied, std::min(xa(i) + 1, na));
@@ -388,9 +393,7 @@ static mp_status host_merge_pipelined(mp_dtype dtype, const KeyKind& k, const vo
         if (vals && e == cudaSuccess) e = copy_in(b_vals, (char*)dBV, 4, b_lo, b_hi);
         if (e == cudaSuccess) e = cudaEventRecord(ev_in[i], s_in);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s_cut, ev_in[i], 0);
-        if (e == cudaSuccess) e = launch_host_cut(k, dA, na, xa(i), dB, nb, yb(i), dcut + 2 * i, s_cut);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(h_cut + 2 * i, dcut + 2 * i, 16, cudaMemcpyDeviceToHost, s_cut);
+        if (e == cudaSuccess) e = launch_host_cut(k, dA, na, xa(i), dB, nb, yb(i), h_cut_dev + 2 * i, s_cut);
         if (e == cudaSuccess) e = cudaEventRecord(ev_cut[i], s_cut);
     }
     // Merge and copy out each settled piece of the output as soon as its cut

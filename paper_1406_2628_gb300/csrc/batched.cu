@@ -1,4 +1,4 @@
-// batched.cu -- many independent merges in one persistent launch.
+// batched.cu -- many independent merges in one launch.
 //
 // Segment s merges A_s = a[a_off[s]..a_off[s+1]) with B_s = b[b_off[s]..
 // b_off[s+1]) into out at c(s) = a_off[s] + b_off[s].  Concatenated, the
@@ -9,7 +9,8 @@
 //
 //   partition  for each tile boundary d: the segment s holding output d
 //              (upper bound of d in c(.)), then Alg. 2 inside that segment.
-//   merge      persistent CTAs walk the tiles; each stages its contiguous
+//   merge      one CTA per tile (TMA staging; register staging loops over a
+//              resident grid); each stages its contiguous
 //              A and B windows, each thread finds its segment (upper bound
 //              in c over the tile's few segments) and its split inside the
 //              window, then merges VT outputs, stepping to the next segment
@@ -304,7 +305,11 @@ static cudaError_t launch_batched_t(const BatchedProblem& q, int64_t* a_split, i
         p, T, n_bounds, a_split, seg_split);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int64_t grid = std::min<int64_t>(p.ntiles, (int64_t)num_sms * blocks_per_sm);
+    // One launch over every segment.  TMA-staged tiles go one per CTA (the
+    // hardware starts a CTA as soon as one retires, overlapping one tile's
+    // copies with other tiles' merges); register-staged tiles loop over a
+    // resident grid.
+    const int64_t grid = BULK ? p.ntiles : std::min<int64_t>(p.ntiles, (int64_t)num_sms * blocks_per_sm);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(NT);

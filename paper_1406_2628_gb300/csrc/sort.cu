@@ -25,10 +25,10 @@ __global__ void __launch_bounds__(NT) block_sort_kernel(const K* in, const uint3
 }
 
 // Block-sort tile shape per key width.
-static constexpr int BS_NT = 256;
-static constexpr int BS_VT4 = 16;  // 4-byte keys: tile 4096
-static constexpr int BS_VT8 = 8;   // 8-byte keys: tile 2048
-static constexpr int BS_VT16 = 4;  // 16-byte keys: tile 1024
+static constexpr int BS_NT = 512;
+static constexpr int BS_VT4 = 16;  // 4-byte keys: tile 8192
+static constexpr int BS_VT8 = 8;   // 8-byte keys: tile 4096
+static constexpr int BS_VT16 = 4;  // 16-byte keys: tile 2048
 
 static int64_t block_tile(int key_bytes)
 {
