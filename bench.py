@@ -67,7 +67,7 @@ def parse_args():
     p.add_argument("--plan", default=None, help="NT,VT tile plan (default: automatic)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the other workloads (plain keys, sort, batched, serving)")
-    p.add_argument("--extras", default="plain,sort,batched,serving,setops,wide",
+    p.add_argument("--extras", default="plain,sort,batched,serving,setops,wide,crossover",
                    help="comma list of extra workloads to run after the headline")
     p.add_argument("--serving-requests", type=int, default=50000)
     return p.parse_args()
@@ -314,6 +314,45 @@ def extra_plain(mp, torch, dev, reps=50):
             "warm_us": warm_us, "cold_us": cold_us, "gkeys_s_warm": n / warm_us / 1e3,
             "gkeys_s_cold": n / cold_us / 1e3, "gbs_cold": 2 * n * 4 / cold_us / 1e3,
             "partitioned_cold_us": statistics.median(tcold)}
+
+
+def extra_crossover(mp, torch, dev, reps=15):
+    """Small merges: the streaming plan (one launch) against partition + TMA
+    tiles, sorted uniform keys, L2 flushed before each call (median of reps),
+    at 2^16 .. 2^24 outputs, int32 keys and uint64 keys with values."""
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    e0, e1 = _events(torch)
+    res = {}
+    for name, kd, vals in [("i32", torch.int32, False), ("u64_pairs", torch.int64, True)]:
+        for lg in (16, 18, 20, 21, 22, 23, 24):
+            n = 1 << (lg - 1)
+            g = torch.Generator(device=dev)
+            g.manual_seed(lg)
+            x = torch.sort(torch.randint(0, 1 << 30, (n,), device=dev, dtype=kd, generator=g)).values
+            y = torch.sort(torch.randint(0, 1 << 30, (n,), device=dev, dtype=kd, generator=g)).values
+            o = torch.empty(2 * n, dtype=kd, device=dev)
+            xv = torch.arange(n, dtype=torch.int32, device=dev)
+            ov = torch.empty(2 * n, dtype=torch.int32, device=dev)
+            row = {}
+            for plan_name, plan in [("stream", (0, 0, mp.MP_STAGE_STREAM)), ("tiles", (0, 0, mp.MP_STAGE_BULK))]:
+                def call():
+                    if vals:
+                        mp.mp_merge_plan(x, y, xv, xv, o, ov, plan=plan)
+                    else:
+                        mp.mp_merge_plan(x, y, out_keys=o, plan=plan)
+                for _ in range(3):
+                    call()
+                ts = []
+                for _ in range(reps):
+                    flush.fill_(1)
+                    e0.record()
+                    call()
+                    e1.record()
+                    torch.cuda.synchronize(dev)
+                    ts.append(e0.elapsed_time(e1) * 1e3)
+                row[plan_name + "_us"] = statistics.median(ts)
+            res[f"{name}_2^{lg}"] = row
+    return res
 
 
 def extra_wide(mp, torch, dev, log2_n=25, reps=5):
@@ -807,7 +846,8 @@ def run_ours(args):
                    "batched": lambda: extra_batched(mp, torch, dev),
                    "serving": lambda: extra_serving(mp, torch, dev, n_req=args.serving_requests),
                    "setops": lambda: extra_setops(mp, torch, dev),
-                   "wide": lambda: extra_wide(mp, torch, dev)}
+                   "wide": lambda: extra_wide(mp, torch, dev),
+                   "crossover": lambda: extra_crossover(mp, torch, dev)}
         del OK, OV
         for name in wanted:
             t0 = time.perf_counter()
