@@ -70,6 +70,8 @@ def parse_args():
     p.add_argument("--extras", default="plain,sort,batched,serving,setops,wide,crossover",
                    help="comma list of extra workloads to run after the headline")
     p.add_argument("--serving-requests", type=int, default=50000)
+    p.add_argument("--sort-log2-n", type=int, default=28, help="keys of the sort extra (log2)")
+    p.add_argument("--batched-segments", type=int, default=16384, help="segments of the batched extra")
     return p.parse_args()
 
 
@@ -842,8 +844,8 @@ def run_ours(args):
         extras = {}
         wanted = [x for x in args.extras.split(",") if x]
         runners = {"plain": lambda: extra_plain(mp, torch, dev),
-                   "sort": lambda: extra_sort(mp, torch, dev),
-                   "batched": lambda: extra_batched(mp, torch, dev),
+                   "sort": lambda: extra_sort(mp, torch, dev, n=1 << args.sort_log2_n),
+                   "batched": lambda: extra_batched(mp, torch, dev, n_seg=args.batched_segments),
                    "serving": lambda: extra_serving(mp, torch, dev, n_req=args.serving_requests),
                    "setops": lambda: extra_setops(mp, torch, dev),
                    "wide": lambda: extra_wide(mp, torch, dev),
