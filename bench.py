@@ -746,6 +746,7 @@ def run_ours(args):
 
     # Per-kernel timing on the same stream: partition alone, merge alone.
     tile = mp.mp_merge_tile_items(torch.uint64, True, n, plan)
+    resolved = mp.mp_merge_resolve_plan(torch.uint64, True, n, plan)
     splits = mp.mp_merge_path_partition(A, B, tile)
     torch.cuda.synchronize(dev)
     reps = max(args.steps, 10)
@@ -809,7 +810,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": config_dict(args, world),
         "roofline": {"bound": "hbm", "kernel": "merge_tile_bulk_kernel (TMA-staged merge tiles)",
-                     "plan": {"block_threads": tile // (8 if tile == 2048 else 16) if plan is None else plan[0],
+                     "plan": {"block_threads": resolved[0], "items_per_thread": resolved[1],
+                              "staging": {1: "vector", 2: "bulk", 3: "warp", 4: "stream"}.get(resolved[2]),
                               "tile": tile},
                      "achieved": achieved,
                      "peak": peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy)",

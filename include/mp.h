@@ -177,6 +177,17 @@ MP_API mp_status mp_merge_plan(mp_dtype dtype,
 MP_API int mp_plan_supported(const mp_plan* plan);
 
 /*
+ * mp_merge_resolve_plan -- the shape mp_merge_plan would run for this dtype,
+ * payload choice (with_values != 0), total output length and plan (NULL or
+ * zero fields: automatic, which consults the tuned table and may pick the
+ * streaming plan for small merges).  Writes it to *resolved (staging never
+ * MP_STAGE_AUTO).  MP_ERR_INVALID_ARG for an unsupported plan or a NULL
+ * resolved; MP_ERR_UNSUPPORTED_DTYPE for an unknown dtype.
+ */
+MP_API mp_status mp_merge_resolve_plan(mp_dtype dtype, int with_values, int64_t total, const mp_plan* plan,
+                                       mp_plan* resolved);
+
+/*
  * mp_merge_tile_items -- the tile length T (outputs per CTA) that
  * mp_merge_partitioned uses for this dtype, payload choice, total output
  * length and plan (NULL = automatic; the automatic choice here is always a

@@ -140,6 +140,7 @@ _SIGNATURES = {
     "mp_queue_destroy": ([_P], _I32),
     "mp_generate": ([_I32, _P, _P, _I64, ctypes.c_uint64, ctypes.c_uint64, _I32, ctypes.c_uint32, _P], _I32),
     "mp_set_capacity": ([_I32, _I64, _I64], _I64),
+    "mp_merge_resolve_plan": ([_I32, _I32, _I64, ctypes.POINTER(mp_plan), ctypes.POINTER(mp_plan)], _I32),
     "mp_set_operation": ([_I32, _I32, _P, _P, _I64, _P, _P, _I64, _P, _P, _P, _P], _I32),
 }
 
@@ -343,6 +344,14 @@ def mp_set_operation(op, a_keys, b_keys, a_vals=None, b_vals=None, out_keys=None
         out_keys = out_keys[:n]
         out_vals = out_vals[:n] if pairs else None
     return out_keys, (out_vals if pairs else None), count
+
+
+def mp_merge_resolve_plan(dtype, with_values: bool, total: int, plan=None):
+    """The (block_threads, items_per_thread, staging) mp_merge_plan would run."""
+    code = dtype if isinstance(dtype, int) else _TORCH_DTYPE[dtype]
+    out = mp_plan()
+    _check(lib().mp_merge_resolve_plan(code, 1 if with_values else 0, int(total), _plan(plan), ctypes.byref(out)))
+    return (out.block_threads, out.items_per_thread, out.staging)
 
 
 def mp_merge_tile_items(dtype, with_values: bool, total: int, plan=None) -> int:

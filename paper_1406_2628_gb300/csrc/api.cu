@@ -162,7 +162,7 @@ static mp_status resolve_shape(const KeyKind& k, bool vals, int64_t total, const
         }
     }
     *s = default_merge_shape(k.bytes, vals, total);
-    if (s->staging == MP_STAGE_STREAM) *s = Shape{256, 8, MP_STAGE_BULK};  // tuned, but splits are given
+    if (s->staging == MP_STAGE_STREAM) *s = builtin_merge_shape(k.bytes, vals);  // tuned, but splits are given
     if (plan && plan->staging == MP_STAGE_STREAM) *s = stream_default_shape(k.bytes, vals);
     if (plan) {
         if (plan->reserved != 0) return fail(MP_ERR_INVALID_ARG, "plan.reserved must be 0");
@@ -518,6 +518,19 @@ int mp_plan_supported(const mp_plan* plan)
             plan->staging ? plan->staging : MP_STAGE_VECTOR};
     if (s.staging == MP_STAGE_STREAM) return stream_shape_supported(s) ? 1 : 0;
     return merge_shape_supported(4, false, s) ? 1 : 0;
+}
+
+mp_status mp_merge_resolve_plan(mp_dtype dtype, int with_values, int64_t total, const mp_plan* plan,
+                                mp_plan* resolved)
+{
+    KeyKind k;
+    if (!key_kind(dtype, &k)) return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_merge_resolve_plan: unknown dtype");
+    if (!resolved) return fail(MP_ERR_INVALID_ARG, "mp_merge_resolve_plan: NULL result");
+    Shape s;
+    const mp_status st = resolve_shape(k, with_values != 0, total, plan, &s);
+    if (st != MP_OK) return st;
+    *resolved = mp_plan{s.nt, s.vt, s.staging, 0};
+    return MP_OK;
 }
 
 int64_t mp_merge_tile_items(mp_dtype dtype, int with_values, int64_t total, const mp_plan* plan)

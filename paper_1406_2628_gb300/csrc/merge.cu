@@ -252,7 +252,7 @@ static cudaError_t launch_bulk_t(const MergeProblem& p, const int64_t* a_split, 
 
 // Compiled tile shapes (NT, VT): vector staging and TMA bulk staging.
 #define MP_MERGE_SHAPES(X) X(128, 8) X(256, 8) X(128, 16) X(256, 16) X(512, 8)
-#define MP_BULK_SHAPES(X) X(128, 8) X(256, 8) X(128, 16) X(256, 16)
+#define MP_BULK_SHAPES(X) X(128, 8) X(256, 8) X(128, 12) X(256, 12) X(128, 16) X(256, 16)
 #define MP_WARP_SHAPES(X) X(128, 8) X(256, 8) X(128, 16) X(256, 16)
 // 128-bit keys: TMA-staged tiles only.
 #define MP_WIDE_SHAPES(X) X(128, 8) X(256, 8)
@@ -298,20 +298,29 @@ Shape default_merge_shape(int key_bytes, bool with_values, int64_t total)
 {
     Shape s;
     if (tuned_shape("merge", key_bytes, with_values, total, &s)) return s;
+    return builtin_merge_shape(key_bytes, with_values);
+}
+
+Shape builtin_merge_shape(int key_bytes, bool with_values)
+{
+    Shape s;
     // Shapes with the shortest partition + merge step on GB300 for large
     // merges (tile-shape sweep): TMA-staged tiles throughout (they need no
-    // staging registers, so more CTAs stay resident);
-    // mp_autotune_merge overrides per size class.
+    // staging registers, so more CTAs stay resident).  Twelve outputs per
+    // thread start the threads' serial walks 12 elements apart, which spreads
+    // a warp's shared-memory loads over more banks than 8 or 16 do; only
+    // 4-byte keys without values keep 16 (their partition is the larger
+    // share).  mp_autotune_merge overrides per size class.
     s.staging = MP_STAGE_BULK;
     if (key_bytes == 16) {
         s.nt = 128;
         s.vt = 8;
     } else if (key_bytes == 8) {
-        s.nt = with_values ? 256 : 128;
-        s.vt = with_values ? 8 : 16;
+        s.nt = 256;
+        s.vt = 12;
     } else {
         s.nt = 256;
-        s.vt = with_values ? 8 : 16;
+        s.vt = with_values ? 12 : 16;
     }
     return s;
 }

@@ -65,7 +65,8 @@ std::vector<Shape> stream_shapes();
 // Automatic plans use the streaming merge up to this many outputs.
 int64_t stream_auto_limit(int key_bytes, bool with_values);
 Shape stream_default_shape(int key_bytes, bool with_values);
-Shape default_merge_shape(int key_bytes, bool with_values, int64_t total);
+Shape default_merge_shape(int key_bytes, bool with_values, int64_t total);  // tuned table first
+Shape builtin_merge_shape(int key_bytes, bool with_values);                 // the shipped default
 std::vector<Shape> merge_shapes();
 
 // Autotuner cache (tune.cu): op is "merge" or "batched".

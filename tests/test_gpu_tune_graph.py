@@ -91,3 +91,16 @@ def test_graph_batched_replay():
         torch.cuda.synchronize()
         assert np.array_equal(OUT.cpu().numpy(), ek)
     g.close()
+
+
+def test_resolve_plan_reports_the_shape_that_runs():
+    big = 335_544_320
+    assert mp.mp_merge_resolve_plan(torch.uint64, True, big) == (256, 12, mp.MP_STAGE_BULK)
+    assert mp.mp_merge_resolve_plan(torch.int32, False, big) == (256, 16, mp.MP_STAGE_BULK)
+    small = mp.mp_merge_resolve_plan(torch.int32, False, 1 << 20)
+    assert small[2] == mp.MP_STAGE_STREAM
+    assert mp.mp_merge_resolve_plan(torch.uint64, True, big, (128, 8, mp.MP_STAGE_BULK)) == (128, 8, mp.MP_STAGE_BULK)
+    tile = mp.mp_merge_tile_items(torch.uint64, True, big)
+    assert tile == 256 * 12
+    with pytest.raises(mp.MPError):
+        mp.mp_merge_resolve_plan(torch.uint64, True, big, (100, 3))
