@@ -255,7 +255,7 @@ static cudaError_t launch_bulk_t(const MergeProblem& p, const int64_t* a_split, 
 #define MP_BULK_SHAPES(X) X(128, 8) X(256, 8) X(128, 12) X(256, 12) X(128, 16) X(256, 16)
 #define MP_WARP_SHAPES(X) X(128, 8) X(256, 8) X(128, 16) X(256, 16)
 // 128-bit keys: TMA-staged tiles only.
-#define MP_WIDE_SHAPES(X) X(128, 8) X(256, 8)
+#define MP_WIDE_SHAPES(X) X(128, 8) X(256, 8) X(128, 12)
 
 bool merge_shape_supported(int key_bytes, bool with_values, const Shape& s)
 {
