@@ -46,10 +46,10 @@ METRIC = "merge Gkeys/s & % of HBM peak; batched/served vs per-call on same GPU;
 UNIT = "Gkeys/s"
 NOMINAL_HBM_GBS = 7900.0
 PEAK_FALLBACK_GBS = 6800.0
-KERNEL_SOURCES = ["paper_1406_2628_gb300/csrc/merge.cu", "paper_1406_2628_gb300/csrc/mp_tile.cuh",
+KERNEL_SOURCES = ["paper_1406_2628_gb300/csrc/merge_bulk.cu", "paper_1406_2628_gb300/csrc/mp_tile.cuh",
                   "paper_1406_2628_gb300/csrc/mp_device.cuh", "paper_1406_2628_gb300/csrc/mp_bulk.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "merge_tile_kernel_large_kv_traffic.json")
-SORT_BLOCK_4B = 8192  # keys per block-sort tile for 4-byte keys (the first of the sort's HBM passes)
+SORT_BLOCK_4B = 512 * 33  # keys per block-sort tile for 4-byte keys alone (the first of the sort's HBM passes)
 
 
 def parse_args():

@@ -119,7 +119,7 @@ __device__ __forceinline__ BatchTile batch_tile(const BatchArgs<K>& p, int64_t t
 // split inside the staged window, merge VT outputs (stepping to the next
 // segment when both sides of the current one are used up) and record the
 // outputs' sources.
-template <class K, bool VALS, int NT, int VT>
+template <class K, bool VALS, int NT, int VT, int CK>
 __device__ __forceinline__ void batched_thread_merge(const BatchArgs<K>& p, const BatchTile& bt,
                                                      const TileView<K, VALS, NT, VT>& v)
 {
@@ -129,11 +129,11 @@ __device__ __forceinline__ void batched_thread_merge(const BatchArgs<K>& p, cons
     const int64_t a0 = bt.a0, a1 = bt.a1, b0 = bt.b0, b1 = bt.b1;
     const int diag = tid * VT < L ? tid * VT : L;
     if (diag >= L) return;
-    uint32_t packed[VT / 2];
+    uint32_t packed[(VT + 1) / 2];
     if (bt.s0 == bt.s1) {
         // The whole tile lies in one segment: a plain Merge Path tile.
-        const int ai = smem_diagonal_search(v.sA, la, v.sB, lb, diag, c);
-        serial_merge_indices<K, VT>(v.sA, la, v.sB, lb, ai, diag - ai, c, packed);
+        const int ai = smem_diagonal_search_ck<CK>(v.sA, la, v.sB, lb, diag, c);
+        serial_merge_indices_ck<K, VT, CK>(v.sA, la, v.sB, lb, ai, diag - ai, c, packed);
         put_indices<VT>(v.sidx, packed);
         return;
     }
@@ -155,7 +155,7 @@ __device__ __forceinline__ void batched_thread_merge(const BatchArgs<K>& p, cons
     const K* sBs = v.sB + (bS - b0);
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
-        if (key_enc(sAs[mid], c) > key_enc(sBs[dl - 1 - mid], c))
+        if (key_enc_ck<CK>(sAs[mid], c) > key_enc_ck<CK>(sBs[dl - 1 - mid], c))
             hi = mid;
         else
             lo = mid + 1;
@@ -167,8 +167,8 @@ __device__ __forceinline__ void batched_thread_merge(const BatchArgs<K>& p, cons
     int bi = clampi(bS + dl - lo - b0, lb);
     int aEnd = clampi((aE < a1 ? aE : a1) - a0, la);
     int bEnd = clampi((bE < b1 ? bE : b1) - b0, lb);
-    K ka = key_enc(v.sA[ai], c);
-    K kb = key_enc(v.sB[bi], c);
+    K ka = key_enc_ck<CK>(v.sA[ai], c);
+    K kb = key_enc_ck<CK>(v.sB[bi], c);
 #pragma unroll
     for (int i = 0; i < VT; ++i) {
         uint32_t src = 0;
@@ -184,7 +184,7 @@ __device__ __forceinline__ void batched_thread_merge(const BatchArgs<K>& p, cons
             const bool take_a = ai < aEnd && (bi >= bEnd || !(ka > kb));
             src = take_a ? (uint32_t)ai : (uint32_t)(la + bi);
             const K* nxt = take_a ? (v.sA + (ai < la ? ai + 1 : la)) : (v.sB + (bi < lb ? bi + 1 : lb));
-            const K kn = key_enc(*nxt, c);
+            const K kn = key_enc_ck<CK>(*nxt, c);
             if (take_a) { ka = kn; ++ai; }
             else { kb = kn; ++bi; }
         }
@@ -208,15 +208,16 @@ __global__ void __launch_bounds__(NT) batched_merge_kernel(BatchArgs<K> p)
         const auto v = stage_tile<K, VALS, NT, VT>(smem, p.a + bt.a0, bt.la, p.b + bt.b0, bt.lb,
                                                    VALS ? p.av + bt.a0 : nullptr,
                                                    VALS ? p.bv + bt.b0 : nullptr);
-        batched_thread_merge<K, VALS, NT, VT>(p, bt, v);
+        batched_thread_merge<K, VALS, NT, VT, CODEC_RUNTIME>(p, bt, v);
         __syncthreads();
         store_tile<K, VALS, NT, VT>(v, p.out + bt.d0, VALS ? p.outv + bt.d0 : nullptr);
         __syncthreads();
     }
 }
 
-// Same, with the windows staged by TMA bulk copies (no staging registers).
-template <class K, bool VALS, int NT, int VT>
+// Same, with the windows staged by TMA bulk copies (no staging registers),
+// compiled per key codec (CK).
+template <class K, bool VALS, int NT, int VT, int CK>
 __global__ void __launch_bounds__(NT) batched_merge_bulk_kernel(BatchArgs<K> p, unsigned int* err)
 {
     constexpr int T = NT * VT;
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(NT) batched_merge_bulk_kernel(BatchArgs<K> p, 
         const auto v = stage_view<K, VALS, NT, VT>(t, lay.sk, lay.sv, lay.sidx);
         if (!bulk_stage<K, VALS, NT, VT>(t, v, lay.bar, parity, err)) return;
         parity ^= 1;
-        batched_thread_merge<K, VALS, NT, VT>(p, bt, v);
+        batched_thread_merge<K, VALS, NT, VT, CK>(p, bt, v);
         __syncthreads();
         store_tile<K, VALS, NT, VT>(v, p.out + bt.d0, VALS ? p.outv + bt.d0 : nullptr);
         __syncthreads();
@@ -275,14 +276,17 @@ static BatchArgs<K> make_batch_args(const BatchedProblem& q, int64_t tile, const
     return p;
 }
 
-template <class K, bool VALS, int NT, int VT, bool BULK>
+template <class K, bool VALS, int NT, int VT, bool BULK, int CK = CODEC_RUNTIME>
 static cudaError_t launch_batched_t(const BatchedProblem& q, int64_t* a_split, int64_t* seg_split,
                                     cudaStream_t stream)
 {
     using SM = typename std::conditional<BULK, BulkSmem<K, VALS, NT, VT>, TileSmem<K, VALS, NT, VT>>::type;
-    auto kern = BULK ? (void (*)(BatchArgs<K>, unsigned int*))batched_merge_bulk_kernel<K, VALS, NT, VT>
-                     : nullptr;
-    auto kern_v = batched_merge_kernel<K, VALS, NT, VT>;
+    void (*kern)(BatchArgs<K>, unsigned int*) = nullptr;
+    void (*kern_v)(BatchArgs<K>) = nullptr;
+    if constexpr (BULK)
+        kern = batched_merge_bulk_kernel<K, VALS, NT, VT, CK>;
+    else
+        kern_v = batched_merge_kernel<K, VALS, NT, VT>;
     static int blocks_per_sm = 0;
     static int num_sms = 0;
     if (blocks_per_sm == 0) {
@@ -329,15 +333,34 @@ static cudaError_t launch_batched_t(const BatchedProblem& q, int64_t* a_split, i
     }
 }
 
+// Tile shapes: register-staged and TMA-staged (MP_BATCHED_SHAPES), and
+// TMA-staged only (MP_BATCHED_BULK_SHAPES: odd items per thread).
 #define MP_BATCHED_SHAPES(X) X(128, 8) X(256, 8) X(128, 12) X(256, 12) X(128, 16) X(256, 16)
+#define MP_BATCHED_BULK_SHAPES(X) X(128, 27) X(128, 33)
 
 static bool batched_shape_supported(const Shape& s)
 {
     if (s.staging != MP_STAGE_VECTOR && s.staging != MP_STAGE_BULK) return false;
 #define X(NT_, VT_) if (s.nt == NT_ && s.vt == VT_) return true;
     MP_BATCHED_SHAPES(X)
+    if (s.staging == MP_STAGE_BULK) {
+        MP_BATCHED_BULK_SHAPES(X)
+    }
 #undef X
     return false;
+}
+
+// TMA-staged launch with the key codec fixed at compile time where it can
+// be (unsigned keys, signed integers); other kinds use the runtime codec.
+template <class K, bool VALS, int NT, int VT>
+static cudaError_t launch_batched_bulk(const BatchedProblem& q, int64_t* a_split, int64_t* seg_split,
+                                       cudaStream_t stream)
+{
+    if (q.kind.identity())
+        return launch_batched_t<K, VALS, NT, VT, true, CODEC_IDENTITY>(q, a_split, seg_split, stream);
+    if (q.kind.signed_int())
+        return launch_batched_t<K, VALS, NT, VT, true, CODEC_SIGNED>(q, a_split, seg_split, stream);
+    return launch_batched_t<K, VALS, NT, VT, true, CODEC_RUNTIME>(q, a_split, seg_split, stream);
 }
 
 static cudaError_t launch_batched(const BatchedProblem& q, const Shape& s, int64_t* a_split,
@@ -349,18 +372,28 @@ static cudaError_t launch_batched(const BatchedProblem& q, const Shape& s, int64
     if (s.nt == NT_ && s.vt == VT_) {                                                                  \
         if (q.kind.bytes == 4) {                                                                       \
             if (bulk)                                                                                  \
-                return vals ? launch_batched_t<uint32_t, true, NT_, VT_, true>(q, a_split, seg_split, stream)   \
-                            : launch_batched_t<uint32_t, false, NT_, VT_, true>(q, a_split, seg_split, stream); \
+                return vals ? launch_batched_bulk<uint32_t, true, NT_, VT_>(q, a_split, seg_split, stream)   \
+                            : launch_batched_bulk<uint32_t, false, NT_, VT_>(q, a_split, seg_split, stream); \
             return vals ? launch_batched_t<uint32_t, true, NT_, VT_, false>(q, a_split, seg_split, stream)      \
                         : launch_batched_t<uint32_t, false, NT_, VT_, false>(q, a_split, seg_split, stream);    \
         }                                                                                              \
         if (bulk)                                                                                      \
-            return vals ? launch_batched_t<uint64_t, true, NT_, VT_, true>(q, a_split, seg_split, stream)       \
-                        : launch_batched_t<uint64_t, false, NT_, VT_, true>(q, a_split, seg_split, stream);     \
+            return vals ? launch_batched_bulk<uint64_t, true, NT_, VT_>(q, a_split, seg_split, stream)       \
+                        : launch_batched_bulk<uint64_t, false, NT_, VT_>(q, a_split, seg_split, stream);     \
         return vals ? launch_batched_t<uint64_t, true, NT_, VT_, false>(q, a_split, seg_split, stream)          \
                     : launch_batched_t<uint64_t, false, NT_, VT_, false>(q, a_split, seg_split, stream);        \
     }
     MP_BATCHED_SHAPES(X)
+#undef X
+#define X(NT_, VT_)                                                                                    \
+    if (bulk && s.nt == NT_ && s.vt == VT_) {                                                          \
+        if (q.kind.bytes == 4)                                                                         \
+            return vals ? launch_batched_bulk<uint32_t, true, NT_, VT_>(q, a_split, seg_split, stream)       \
+                        : launch_batched_bulk<uint32_t, false, NT_, VT_>(q, a_split, seg_split, stream);     \
+        return vals ? launch_batched_bulk<uint64_t, true, NT_, VT_>(q, a_split, seg_split, stream)           \
+                    : launch_batched_bulk<uint64_t, false, NT_, VT_>(q, a_split, seg_split, stream);         \
+    }
+    MP_BATCHED_BULK_SHAPES(X)
 #undef X
     return cudaErrorInvalidValue;
 }
@@ -392,12 +425,14 @@ mp_status batched_prepare(mp_dtype dtype, const void* a, const int64_t* a_off, c
         return fail(MP_ERR_INVALID_ARG, "mp_merge_batched: value pointer not 4-byte aligned");
 
     if (!tuned_shape("batched", k.bytes, vals, na_total + nb_total, s)) {
-        // Tiles of 128 x 12: the batched tile's walks (segment lookups and
-        // the serial merge) are bound by the shared-memory pipe, and 12
-        // outputs per thread spread them over more banks (16,384 segments:
-        // 1.23 ms against 1.63 ms for 256 x 16).
+        // Tiles of 128 x 33: the batched tile's walks (segment lookups and
+        // the serial merge) are bound by the shared-memory pipe; an odd
+        // number of outputs per thread starts the threads' walks in
+        // different banks and spreads each thread's search over more
+        // outputs (16,384 int32 segments: 1.11 ms, against 1.17 ms for
+        // 128 x 12 and 1.63 ms for 256 x 16).
         s->nt = 128;
-        s->vt = 12;
+        s->vt = 33;
         s->staging = MP_STAGE_BULK;
     }
     if (plan) {
@@ -442,6 +477,9 @@ std::vector<Shape> batched_shapes()
     std::vector<Shape> v;
 #define X(NT_, VT_) v.push_back(Shape{NT_, VT_, MP_STAGE_VECTOR}); v.push_back(Shape{NT_, VT_, MP_STAGE_BULK});
     MP_BATCHED_SHAPES(X)
+#undef X
+#define X(NT_, VT_) v.push_back(Shape{NT_, VT_, MP_STAGE_BULK});
+    MP_BATCHED_BULK_SHAPES(X)
 #undef X
     return v;
 }

@@ -56,15 +56,6 @@ __global__ void __launch_bounds__(NT) merge_tile_warp_kernel(TileArgs<K> p, unsi
     merge_tile_warp_body<K, VALS, NT, VT, CK>(p, blockIdx.x, p.a_split, smem, err);
 }
 
-// Variant whose windows are staged by TMA bulk copies (one tile per CTA).
-template <class K, bool VALS, int NT, int VT, int CK>
-__global__ void __launch_bounds__(NT) merge_tile_bulk_kernel(TileArgs<K> p, unsigned int* err)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    merge_tile_bulk_body<K, VALS, NT, VT, CK>(p, blockIdx.x, p.a_split, smem, err);
-}
-
 // Sum of n partial digests into *sum (one CTA).
 __global__ void __launch_bounds__(1024) sum_partials_kernel(const unsigned long long* partial, int64_t n,
                                                             unsigned long long* sum)
@@ -109,25 +100,6 @@ unsigned int* kernel_error_word()
 // ---------------------------------------------------------------------------
 // Host side.
 // ---------------------------------------------------------------------------
-template <class K>
-static TileArgs<K> make_args(const MergeProblem& p, const int64_t* a_split)
-{
-    TileArgs<K> t;
-    t.a = static_cast<const K*>(p.a);
-    t.b = static_cast<const K*>(p.b);
-    t.av = p.av;
-    t.bv = p.bv;
-    t.out = static_cast<K*>(p.out);
-    t.outv = p.outv;
-    t.na = p.na;
-    t.nb = p.nb;
-    t.run = p.run;
-    t.total = p.total();
-    t.a_split = a_split;
-    t.codec = make_codec<K>(p.kind.flip, p.kind.fmask, p.kind.inv);
-    return t;
-}
-
 cudaError_t launch_partition(const MergeProblem& p, int64_t spacing, int64_t* a_split,
                              cudaStream_t stream)
 {
@@ -136,13 +108,13 @@ cudaError_t launch_partition(const MergeProblem& p, int64_t spacing, int64_t* a_
     const int64_t blocks = ceil_div(n_bounds, threads);
     if (p.kind.bytes == 4)
         partition_kernel<uint32_t><<<(unsigned)blocks, threads, 0, stream>>>(
-            make_args<uint32_t>(p, nullptr), spacing, n_bounds, a_split);
+            make_tile_args<uint32_t>(p, nullptr), spacing, n_bounds, a_split);
     else if (p.kind.bytes == 8)
         partition_kernel<uint64_t><<<(unsigned)blocks, threads, 0, stream>>>(
-            make_args<uint64_t>(p, nullptr), spacing, n_bounds, a_split);
+            make_tile_args<uint64_t>(p, nullptr), spacing, n_bounds, a_split);
     else
         partition_kernel<u128><<<(unsigned)blocks, threads, 0, stream>>>(
-            make_args<u128>(p, nullptr), spacing, n_bounds, a_split);
+            make_tile_args<u128>(p, nullptr), spacing, n_bounds, a_split);
     return cudaGetLastError();
 }
 
@@ -169,7 +141,7 @@ static cudaError_t launch_tiles_ck(const MergeProblem& p, const int64_t* a_split
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, make_args<K>(p, a_split));
+    return cudaLaunchKernelEx(&cfg, kern, make_tile_args<K>(p, a_split));
 }
 
 // Unsigned keys compare as they are; other dtypes go through the codec.
@@ -179,33 +151,6 @@ static cudaError_t launch_tiles_t(const MergeProblem& p, const int64_t* a_split,
     if (p.kind.identity())
         return launch_tiles_ck<K, VALS, NT, VT, CODEC_IDENTITY>(p, a_split, stream);
     return launch_tiles_ck<K, VALS, NT, VT, CODEC_RUNTIME>(p, a_split, stream);
-}
-
-template <class K, bool VALS, int NT, int VT, int CK>
-static cudaError_t launch_bulk_ck(const MergeProblem& p, const int64_t* a_split, cudaStream_t stream)
-{
-    using SM = BulkSmem<K, VALS, NT, VT>;
-    auto kern = merge_tile_bulk_kernel<K, VALS, NT, VT, CK>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    unsigned int* err = kernel_error_word();
-    if (!err) return cudaErrorInvalidSymbol;
-    const int64_t tiles = ceil_div(p.total(), (int64_t)NT * VT);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)tiles);
-    cfg.blockDim = dim3(NT);
-    cfg.dynamicSmemBytes = SM::bytes;
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, make_args<K>(p, a_split), err);
 }
 
 template <class K, bool VALS, int NT, int VT, int CK>
@@ -232,7 +177,7 @@ static cudaError_t launch_warp_ck(const MergeProblem& p, const int64_t* a_split,
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, make_args<K>(p, a_split), err);
+    return cudaLaunchKernelEx(&cfg, kern, make_tile_args<K>(p, a_split), err);
 }
 
 template <class K, bool VALS, int NT, int VT>
@@ -242,20 +187,11 @@ static cudaError_t launch_warp_t(const MergeProblem& p, const int64_t* a_split, 
     return launch_warp_ck<K, VALS, NT, VT, CODEC_RUNTIME>(p, a_split, stream);
 }
 
-template <class K, bool VALS, int NT, int VT>
-static cudaError_t launch_bulk_t(const MergeProblem& p, const int64_t* a_split, cudaStream_t stream)
-{
-    if (p.kind.identity())
-        return launch_bulk_ck<K, VALS, NT, VT, CODEC_IDENTITY>(p, a_split, stream);
-    return launch_bulk_ck<K, VALS, NT, VT, CODEC_RUNTIME>(p, a_split, stream);
-}
-
-// Compiled tile shapes (NT, VT): vector staging and TMA bulk staging.
+// Compiled tile shapes (NT, VT) of the register-staged and warp-cooperative
+// tiles.  The TMA bulk shapes (MP_BULK_SHAPES, MP_WIDE_SHAPES) are listed in
+// mp_internal.h; their kernels live in merge_bulk.cu.
 #define MP_MERGE_SHAPES(X) X(128, 8) X(256, 8) X(128, 16) X(256, 16) X(512, 8)
-#define MP_BULK_SHAPES(X) X(128, 8) X(256, 8) X(128, 12) X(256, 12) X(128, 16) X(256, 16)
 #define MP_WARP_SHAPES(X) X(128, 8) X(256, 8) X(128, 16) X(256, 16)
-// 128-bit keys: TMA-staged tiles only.
-#define MP_WIDE_SHAPES(X) X(128, 8) X(256, 8) X(128, 12)
 
 bool merge_shape_supported(int key_bytes, bool with_values, const Shape& s)
 {
@@ -305,22 +241,27 @@ Shape builtin_merge_shape(int key_bytes, bool with_values)
 {
     Shape s;
     // Shapes with the shortest partition + merge step on GB300 for large
-    // merges (tile-shape sweep): TMA-staged tiles throughout (they need no
-    // staging registers, so more CTAs stay resident).  Twelve outputs per
-    // thread start the threads' serial walks 12 elements apart, which spreads
-    // a warp's shared-memory loads over more banks than 8 or 16 do; only
-    // 4-byte keys without values keep 16 (their partition is the larger
-    // share).  mp_autotune_merge overrides per size class.
+    // merges (tile-shape sweep), all TMA-staged (no staging registers, so
+    // more CTAs stay resident).  An odd number of outputs per thread starts
+    // the threads' serial walks in different shared-memory banks and, with
+    // more outputs per thread, spreads each thread's diagonal search over
+    // more outputs: 4-byte keys alone take 256 x 33, 8-byte keys alone
+    // 128 x 27.  Keys with values keep 12 per thread (256 x 12), where the
+    // larger tile would leave fewer CTAs per SM.  mp_autotune_merge
+    // overrides per size class.
     s.staging = MP_STAGE_BULK;
     if (key_bytes == 16) {
         s.nt = 128;
-        s.vt = 8;
-    } else if (key_bytes == 8) {
+        s.vt = 12;
+    } else if (with_values) {
         s.nt = 256;
         s.vt = 12;
+    } else if (key_bytes == 8) {
+        s.nt = 128;
+        s.vt = 27;
     } else {
         s.nt = 256;
-        s.vt = with_values ? 12 : 16;
+        s.vt = 33;
     }
     return s;
 }
@@ -329,16 +270,7 @@ cudaError_t launch_merge_tiles(const MergeProblem& p, const Shape& s, const int6
                                cudaStream_t stream)
 {
     const bool vals = p.vals;
-    if (p.kind.bytes == 16) {
-        if (s.staging != MP_STAGE_BULK) return cudaErrorInvalidValue;
-#define X(NT_, VT_)                                                                            \
-        if (s.nt == NT_ && s.vt == VT_)                                                        \
-            return vals ? launch_bulk_t<u128, true, NT_, VT_>(p, a_split, stream)              \
-                        : launch_bulk_t<u128, false, NT_, VT_>(p, a_split, stream);
-        MP_WIDE_SHAPES(X)
-#undef X
-        return cudaErrorInvalidValue;
-    }
+    if (p.kind.bytes == 16 || s.staging == MP_STAGE_BULK) return launch_merge_bulk(p, s, a_split, stream);
     if (s.staging == MP_STAGE_WARP) {
 #define X(NT_, VT_)                                                                            \
         if (s.nt == NT_ && s.vt == VT_) {                                                      \
@@ -349,19 +281,6 @@ cudaError_t launch_merge_tiles(const MergeProblem& p, const Shape& s, const int6
                         : launch_warp_t<uint64_t, false, NT_, VT_>(p, a_split, stream);        \
         }
         MP_WARP_SHAPES(X)
-#undef X
-        return cudaErrorInvalidValue;
-    }
-    if (s.staging == MP_STAGE_BULK) {
-#define X(NT_, VT_)                                                                            \
-        if (s.nt == NT_ && s.vt == VT_) {                                                      \
-            if (p.kind.bytes == 4)                                                             \
-                return vals ? launch_bulk_t<uint32_t, true, NT_, VT_>(p, a_split, stream)      \
-                            : launch_bulk_t<uint32_t, false, NT_, VT_>(p, a_split, stream);    \
-            return vals ? launch_bulk_t<uint64_t, true, NT_, VT_>(p, a_split, stream)          \
-                        : launch_bulk_t<uint64_t, false, NT_, VT_>(p, a_split, stream);        \
-        }
-        MP_BULK_SHAPES(X)
 #undef X
         return cudaErrorInvalidValue;
     }
@@ -413,7 +332,7 @@ static cudaError_t launch_checksum_t(const MergeProblem& p, const int64_t* a_spl
     unsigned int* err = kernel_error_word();
     if (!err) return cudaErrorInvalidSymbol;
     const int64_t tiles = ceil_div(p.total(), (int64_t)NT * VT);
-    kern<<<(unsigned)tiles, NT, SM::bytes, stream>>>(make_args<K>(p, a_split), err, partial);
+    kern<<<(unsigned)tiles, NT, SM::bytes, stream>>>(make_tile_args<K>(p, a_split), err, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     sum_partials_kernel<<<1, 1024, 0, stream>>>(partial, tiles, sum);

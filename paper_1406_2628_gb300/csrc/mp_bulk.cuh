@@ -265,7 +265,7 @@ __device__ __forceinline__ void merge_tile_bulk_body(const TileArgs<K>& p, int64
     {
         const int diag = tid * VT < L ? tid * VT : L;
         const int ai = smem_diagonal_search_ck<CK>(v.sA, t.la, v.sB, t.lb, diag, p.codec);
-        uint32_t packed[VT / 2];
+        uint32_t packed[(VT + 1) / 2];
         serial_merge_indices_ck<K, VT, CK>(v.sA, t.la, v.sB, t.lb, ai, diag - ai, p.codec, packed);
         put_indices<VT>(lay.sidx, packed);
     }
@@ -306,7 +306,7 @@ __device__ __forceinline__ void merge_tile_checksum_body(const TileArgs<K>& p, i
     const int L = t.la + t.lb;
     const int diag = tid * VT < L ? tid * VT : L;
     const int ai = smem_diagonal_search_ck<CK>(v.sA, t.la, v.sB, t.lb, diag, p.codec);
-    uint32_t packed[VT / 2];
+    uint32_t packed[(VT + 1) / 2];
     serial_merge_indices_ck<K, VT, CK>(v.sA, t.la, v.sB, t.lb, ai, diag - ai, p.codec, packed);
     uint64_t acc = 0;
 #pragma unroll

@@ -76,15 +76,26 @@ __host__ __device__ inline Codec<K> make_codec(uint64_t flip, uint64_t fmask, ui
 }
 
 // Codec kinds known at compile time: identity (unsigned keys: the
-// comparison needs no encoding at all) or the runtime flip/fmask codec.
-enum { CODEC_IDENTITY = 0, CODEC_RUNTIME = 1 };
+// comparison needs no encoding at all), signed integers (the top bit
+// flipped), ascending floats (the top bit of positives flipped, every bit of
+// negatives) and the runtime flip/fmask/inv codec (descending order).  Each
+// fixed kind computes key_enc with its codec's constants folded in.
+enum { CODEC_IDENTITY = 0, CODEC_RUNTIME = 1, CODEC_SIGNED = 2, CODEC_FLOAT = 3 };
 
 template <int CK, class K>
 __device__ __forceinline__ K key_enc_ck(K x, Codec<K> c)
 {
+    constexpr K top = (K)1 << (8 * sizeof(K) - 1);
     if constexpr (CK == CODEC_IDENTITY) {
         (void)c;
         return x;
+    } else if constexpr (CK == CODEC_SIGNED) {
+        (void)c;
+        return x ^ top;
+    } else if constexpr (CK == CODEC_FLOAT) {
+        (void)c;
+        using S = signed_of<K>;
+        return x ^ ((K)((S)x >> (8 * sizeof(K) - 1)) | top);
     } else {
         return key_enc(x, c);
     }
@@ -302,7 +313,7 @@ __device__ __forceinline__ int smem_diagonal_search_enc(const K* sA, int la, con
 template <class K, int VT>
 __device__ __forceinline__ void serial_merge_indices(const K* sA, int la, const K* sB, int lb,
                                                      int ai, int bi, Codec<K> c,
-                                                     uint32_t (&packed)[VT / 2])
+                                                     uint32_t (&packed)[(VT + 1) / 2])
 {
     K ka = key_enc(sA[ai], c);
     K kb = key_enc(sB[bi], c);
@@ -342,7 +353,7 @@ __device__ __forceinline__ int smem_diagonal_search_ck(const K* sA, int la, cons
 template <class K, int VT, int CK>
 __device__ __forceinline__ void serial_merge_indices_ck(const K* sA, int la, const K* sB, int lb,
                                                         int ai, int bi, Codec<K> c,
-                                                        uint32_t (&packed)[VT / 2])
+                                                        uint32_t (&packed)[(VT + 1) / 2])
 {
     K ka = key_enc_ck<CK>(sA[ai], c);
     K kb = key_enc_ck<CK>(sB[bi], c);

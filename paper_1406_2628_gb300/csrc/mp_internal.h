@@ -18,6 +18,9 @@ struct KeyKind {
     uint64_t fmask;  // all ones for float keys
     uint64_t inv;    // all ones for descending order (MP_DESCENDING)
     bool identity() const { return flip == 0 && fmask == 0 && inv == 0; }
+    // Ascending signed integers / ascending floats (fixed codecs).
+    bool signed_int() const { return flip != 0 && fmask == 0 && inv == 0; }
+    bool ascending_float() const { return fmask != 0 && inv == 0; }
 };
 bool key_kind(mp_dtype dtype, KeyKind* out);
 
@@ -58,6 +61,12 @@ cudaError_t launch_partition(const MergeProblem& p, int64_t spacing, int64_t* a_
 cudaError_t launch_merge_tiles(const MergeProblem& p, const Shape& shape, const int64_t* a_split,
                                cudaStream_t stream);
 bool merge_shape_supported(int key_bytes, bool with_values, const Shape& shape);
+// The TMA-staged tile kernels (merge_bulk.cu): 4- and 8-byte keys in the
+// MP_BULK_SHAPES, 16-byte keys in the MP_WIDE_SHAPES (NT, VT).
+#define MP_BULK_SHAPES(X) X(128, 8) X(256, 8) X(128, 12) X(256, 12) X(128, 16) X(256, 16) X(128, 27) X(128, 33) X(256, 33)
+#define MP_WIDE_SHAPES(X) X(128, 8) X(256, 8) X(128, 12)
+cudaError_t launch_merge_bulk(const MergeProblem& p, const Shape& shape, const int64_t* a_split,
+                              cudaStream_t stream);
 // Partition-free streaming merge (stream.cu): one launch, no scratch.
 cudaError_t launch_merge_stream(const MergeProblem& p, const Shape& shape, cudaStream_t stream);
 bool stream_shape_supported(const Shape& shape);

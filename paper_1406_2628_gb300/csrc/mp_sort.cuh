@@ -10,9 +10,10 @@
 //      merge pairwise, each thread producing VT outputs of its pair after a
 //      diagonal search (Alg. 2) in that pair;
 //   4. coalesced store (keys decoded; values gathered by source position).
-// Shared arrays are padded by one element per 128 bytes, so the
-// thread-major accesses (thread t touching elements t*VT .. t*VT+VT-1) and
-// the strided reads of the merge rounds spread over the banks.
+// With VT even, shared arrays are padded by one element per 128 bytes, so
+// the thread-major accesses (thread t touching elements t*VT .. t*VT+VT-1)
+// and the strided reads of the merge rounds spread over the banks; with VT
+// odd the thread-major stride itself does, and the arrays are not padded.
 #pragma once
 
 #include "mp_device.cuh"
@@ -27,17 +28,21 @@ constexpr int per128_log2()
     return sizeof(E) == 16 ? 3 : (sizeof(E) == 8 ? 4 : (sizeof(E) == 4 ? 5 : 6));
 }
 
-template <class E>
+template <class E, bool PAD = true>
 __device__ __forceinline__ int padded(int i)
 {
-    return i + (i >> per128_log2<E>());
+    if constexpr (PAD)
+        return i + (i >> per128_log2<E>());
+    else
+        return i;
 }
 
 template <class K, bool VALS, int NT, int VT>
 struct SortSmem {
     static constexpr int T = NT * VT;
-    static constexpr int KEYS = T + (T >> per128_log2<K>()) + 1;
-    static constexpr int TAGS = VALS ? T + T / 64 + 2 : 0;
+    static constexpr bool PAD = VT % 2 == 0;
+    static constexpr int KEYS = T + (PAD ? (T >> per128_log2<K>()) : 0) + 1;
+    static constexpr int TAGS = VALS ? T + (PAD ? T / 64 : 0) + 2 : 0;
     static constexpr size_t keys_bytes = ((size_t)KEYS * sizeof(K) + 15) / 16 * 16;
     static constexpr size_t tags_bytes = ((size_t)TAGS * 2 + 15) / 16 * 16;
     static constexpr size_t vals_bytes = VALS ? (size_t)T * 4 : 0;
@@ -58,8 +63,10 @@ __device__ __forceinline__ void cmp_swap(K (&k)[VT], uint16_t (&g)[VT], int a, i
     }
 }
 
-// Batcher's odd-even merge sort network on n (a power of two) elements, as
-// a compile-time list of comparator pairs (a < b).
+// Batcher's odd-even merge sort network on n elements, as a compile-time
+// list of comparator pairs (a < b).  For n not a power of two it is the
+// network of the next power of two with the comparators that reach past n
+// left out (as if the missing inputs were +infinity).
 constexpr int batcher_count(int n)
 {
     int c = 0;
@@ -106,8 +113,9 @@ __device__ __forceinline__ void block_sort_body(const K* in, const uint32_t* vin
                                                 uint32_t* vout, int64_t n, Codec<K> c, int64_t tile,
                                                 unsigned char* smem)
 {
-    static_assert((VT & (VT - 1)) == 0, "VT must be a power of two");
+    static_assert((NT & (NT - 1)) == 0, "NT must be a power of two");
     using SM = SortSmem<K, VALS, NT, VT>;
+    constexpr bool PAD = SM::PAD;
     constexpr int T = SM::T;
     K* sk = reinterpret_cast<K*>(smem);
     uint16_t* stag = reinterpret_cast<uint16_t*>(smem + SM::keys_bytes);
@@ -121,7 +129,7 @@ __device__ __forceinline__ void block_sort_body(const K* in, const uint32_t* vin
     // 1. Coalesced load; positions past the end hold the padding key.
 #pragma unroll 4
     for (int j = tid; j < T; j += NT) {
-        sk[padded<K>(j)] = j < L ? key_enc(in[base + j], c) : pad;
+        sk[padded<K, PAD>(j)] = j < L ? key_enc(in[base + j], c) : pad;
         if constexpr (VALS) {
             if (j < L) sv[j] = vin[base + j];
         }
@@ -133,63 +141,65 @@ __device__ __forceinline__ void block_sort_body(const K* in, const uint32_t* vin
     uint16_t tags[VT];
 #pragma unroll
     for (int i = 0; i < VT; ++i) {
-        keys[i] = sk[padded<K>(tid * VT + i)];
+        keys[i] = sk[padded<K, PAD>(tid * VT + i)];
         tags[i] = (uint16_t)(tid * VT + i);
     }
     register_sort<K, VALS, VT>(keys, tags);
 
-    // 3. Merge rounds: runs of width w merge pairwise.
-    for (int w = VT; w < T; w *= 2) {
+    // 3. Merge rounds: runs of width w = VT * 2^r merge pairwise; the pair
+    //    of thread tid starts at run 2 * (tid >> (r + 1)).
+    for (int r = 0; (VT << r) < T; ++r) {
+        const int w = VT << r;
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < VT; ++i) {
-            sk[padded<K>(tid * VT + i)] = keys[i];
-            if constexpr (VALS) stag[padded<uint16_t>(tid * VT + i)] = tags[i];
+            sk[padded<K, PAD>(tid * VT + i)] = keys[i];
+            if constexpr (VALS) stag[padded<uint16_t, PAD>(tid * VT + i)] = tags[i];
         }
         __syncthreads();
-        const int gs = (tid * VT) & ~(2 * w - 1);  // start of this thread's run pair
+        const int gs = ((tid >> (r + 1)) << (r + 1)) * VT;  // start of this thread's run pair
         const int diag = tid * VT - gs;
         // Diagonal search (Alg. 2) in the pair A = [gs, gs+w), B = [gs+w, gs+2w).
         int lo = diag - w > 0 ? diag - w : 0;
         int hi = diag < w ? diag : w;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
-            if (sk[padded<K>(gs + mid)] > sk[padded<K>(gs + w + diag - 1 - mid)])
+            if (sk[padded<K, PAD>(gs + mid)] > sk[padded<K, PAD>(gs + w + diag - 1 - mid)])
                 hi = mid;
             else
                 lo = mid + 1;
         }
         // Serial merge of VT outputs (ties take A).
         int ai = lo, bi = diag - lo;
-        K ka = sk[padded<K>(gs + (ai < w ? ai : w - 1))];
-        K kb = sk[padded<K>(gs + w + (bi < w ? bi : w - 1))];
+        K ka = sk[padded<K, PAD>(gs + (ai < w ? ai : w - 1))];
+        K kb = sk[padded<K, PAD>(gs + w + (bi < w ? bi : w - 1))];
 #pragma unroll
         for (int i = 0; i < VT; ++i) {
             const bool take_a = (bi >= w) || (ai < w && !(ka > kb));
             keys[i] = take_a ? ka : kb;
             if constexpr (VALS)
-                tags[i] = stag[padded<uint16_t>(take_a ? gs + ai : gs + w + bi)];
+                tags[i] = stag[padded<uint16_t, PAD>(take_a ? gs + ai : gs + w + bi)];
             if (take_a) {
                 ++ai;
-                ka = sk[padded<K>(gs + (ai < w ? ai : w - 1))];
+                ka = sk[padded<K, PAD>(gs + (ai < w ? ai : w - 1))];
             } else {
                 ++bi;
-                kb = sk[padded<K>(gs + w + (bi < w ? bi : w - 1))];
+                kb = sk[padded<K, PAD>(gs + w + (bi < w ? bi : w - 1))];
             }
         }
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < VT; ++i) {
-        sk[padded<K>(tid * VT + i)] = keys[i];
-        if constexpr (VALS) stag[padded<uint16_t>(tid * VT + i)] = tags[i];
+        sk[padded<K, PAD>(tid * VT + i)] = keys[i];
+        if constexpr (VALS) stag[padded<uint16_t, PAD>(tid * VT + i)] = tags[i];
     }
     __syncthreads();
     // 4. Coalesced store.
 #pragma unroll 4
     for (int j = tid; j < L; j += NT) {
-        out[base + j] = key_dec(sk[padded<K>(j)], c);
-        if constexpr (VALS) vout[base + j] = sv[stag[padded<uint16_t>(j)]];
+        out[base + j] = key_dec(sk[padded<K, PAD>(j)], c);
+        if constexpr (VALS) vout[base + j] = sv[stag[padded<uint16_t, PAD>(j)]];
     }
 }
 

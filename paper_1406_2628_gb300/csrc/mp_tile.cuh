@@ -10,6 +10,7 @@
 #pragma once
 
 #include "mp_device.cuh"
+#include "mp_internal.h"
 
 namespace mp {
 
@@ -26,6 +27,26 @@ struct TileArgs {
     const int64_t* a_split;
     Codec<K> codec;
 };
+
+// Kernel arguments of a merge problem (host side).
+template <class K>
+inline TileArgs<K> make_tile_args(const MergeProblem& p, const int64_t* a_split)
+{
+    TileArgs<K> t;
+    t.a = static_cast<const K*>(p.a);
+    t.b = static_cast<const K*>(p.b);
+    t.av = p.av;
+    t.bv = p.bv;
+    t.out = static_cast<K*>(p.out);
+    t.outv = p.outv;
+    t.na = p.na;
+    t.nb = p.nb;
+    t.run = p.run;
+    t.total = p.total();
+    t.a_split = a_split;
+    t.codec = make_codec<K>(p.kind.flip, p.kind.fmask, p.kind.inv);
+    return t;
+}
 
 // The merge pair that output index d belongs to (run == 0: the only pair).
 template <class K>
@@ -138,12 +159,16 @@ __device__ __forceinline__ TileView<K, VALS, NT, VT> stage_tile(unsigned char* s
     return v;
 }
 
-// Store this thread's VT packed source indices at sidx[tid*VT ...].
+// Store this thread's VT packed source indices at sidx[tid*VT ...]: vector
+// stores when VT is a multiple of 4, else one 16-bit store per output.
 template <int VT>
-__device__ __forceinline__ void put_indices(uint16_t* sidx, const uint32_t (&packed)[VT / 2])
+__device__ __forceinline__ void put_indices(uint16_t* sidx, const uint32_t (&packed)[(VT + 1) / 2])
 {
     const int tid = threadIdx.x;
-    if constexpr (VT % 8 == 0) {
+    if constexpr (VT % 4 != 0) {
+#pragma unroll
+        for (int i = 0; i < VT; ++i) sidx[tid * VT + i] = (uint16_t)(packed[i / 2] >> (16 * (i & 1)));
+    } else if constexpr (VT % 8 == 0) {
 #pragma unroll
         for (int i = 0; i < VT / 8; ++i)
             reinterpret_cast<uint4*>(sidx + tid * VT)[i] =
@@ -171,7 +196,7 @@ __device__ __forceinline__ void store_tile(const TileView<K, VALS, NT, VT>& v, K
     if ((((uintptr_t)gout) & 15) == 0) {
         const int nvec = L / EK;
 #pragma unroll
-        for (int j = 0; j < VT / EK; ++j) {
+        for (int j = 0; j < (VT + EK - 1) / EK; ++j) {
             const int g = tid + j * NT;
             if (g < nvec) {
                 K w[EK];
@@ -199,7 +224,7 @@ __device__ __forceinline__ void store_tile(const TileView<K, VALS, NT, VT>& v, K
         if ((((uintptr_t)gvout) & 15) == 0) {
             const int nvec = L / 4;
 #pragma unroll
-            for (int j = 0; j < VT / 4; ++j) {
+            for (int j = 0; j < (VT + 3) / 4; ++j) {
                 const int g = tid + j * NT;
                 if (g < nvec) {
                     const uint2 pk = *reinterpret_cast<const uint2*>(sidx + g * 4);
@@ -256,7 +281,7 @@ __device__ __forceinline__ void merge_tile_body(const TileArgs<K>& p, int64_t ti
     {
         const int diag = tid * VT < L ? tid * VT : L;
         const int ai = smem_diagonal_search_ck<CK>(v.sA, la, v.sB, lb, diag, p.codec);
-        uint32_t packed[VT / 2];
+        uint32_t packed[(VT + 1) / 2];
         serial_merge_indices_ck<K, VT, CK>(v.sA, la, v.sB, lb, ai, diag - ai, p.codec, packed);
         put_indices<VT>(v.sidx, packed);
     }

@@ -200,7 +200,7 @@ __device__ __noinline__ bool setop_slow(bool from_a, K v, int ai, int bi, const 
 template <class K, int VT, int CK, bool SRC>
 __device__ __forceinline__ uint32_t setop_walk(const K* sA, int la, const K* sB, int lb, int ai, int bi,
                                                int n_valid, int op, const SetCtx<K>& x, int64_t a0,
-                                               int64_t b0, Codec<K> c, uint32_t (&packed)[VT / 2])
+                                               int64_t b0, Codec<K> c, uint32_t (&packed)[(VT + 1) / 2])
 {
     static_assert(VT <= 32, "one bit per output");
     const int ai0 = ai, bi0 = bi;
@@ -284,7 +284,7 @@ __device__ __forceinline__ uint32_t setop_walk(const K* sA, int la, const K* sB,
 template <class K, bool VALS, int NT, int VT, int CK, bool SRC>
 __device__ __forceinline__ bool setop_tile_walk(const SetArgs<K>& p, int64_t tile, unsigned char* smem,
                                                 unsigned int* err, TilePlace<K>& t,
-                                                TileView<K, VALS, NT, VT>& v, uint32_t (&packed)[VT / 2],
+                                                TileView<K, VALS, NT, VT>& v, uint32_t (&packed)[(VT + 1) / 2],
                                                 uint32_t& keep, unsigned long long* place = nullptr)
 {
     using SM = SetSmem<K, VALS, NT, VT>;
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(NT, sizeof(K) == 4 ? 4 : 2) setop_count_kernel
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     TilePlace<K> t;
     TileView<K, VALS, NT, VT> v;
-    uint32_t packed[VT / 2];
+    uint32_t packed[(VT + 1) / 2];
     uint32_t keep = 0;
     if (!setop_tile_walk<K, VALS, NT, VT, CK, false>(p, blockIdx.x, smem, err, t, v, packed, keep, nullptr))
         return;
@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(NT, sizeof(K) == 4 ? 4 : 2) setop_emit_kernel(
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     TilePlace<K> t;
     TileView<K, VALS, NT, VT> v;
-    uint32_t packed[VT / 2];
+    uint32_t packed[(VT + 1) / 2];
     uint32_t keep = 0;
     if (!setop_tile_walk<K, VALS, NT, VT, CK, true>(p, blockIdx.x, smem, err, t, v, packed, keep, &scan[NW + 1]))
         return;

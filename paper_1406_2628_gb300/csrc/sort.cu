@@ -24,28 +24,42 @@ __global__ void __launch_bounds__(NT) block_sort_kernel(const K* in, const uint3
     block_sort_body<K, VALS, NT, VT>(in, vin, out, vout, n, c, blockIdx.x, smem);
 }
 
-// Block-sort tile shape per key width.
-static constexpr int BS_NT = 512;
-static constexpr int BS_VT4 = 16;  // 4-byte keys: tile 8192
-static constexpr int BS_VT8 = 8;   // 8-byte keys: tile 4096
-static constexpr int BS_VT16 = 4;  // 16-byte keys: tile 2048
+// Per sort mode (key width, with or without values): the block-sort tile
+// NT x VT and the merge-pass tile.  A merge tile must divide twice the block
+// tile, so that it lies inside one run pair in every pass.  With an odd
+// number of outputs per thread the threads' runs start in different
+// shared-memory banks (in the block sort and in the passes).  4-byte keys
+// alone use 512 x 33 = 16,896-key blocks (2^28 keys need 14 passes, not the
+// 15 of 8192-key blocks); the modes with values and the 8-byte keys, whose
+// threads hold more registers, sort 256-thread blocks (more CTAs resident
+// per SM), which measured faster than the larger blocks' saved pass.
+struct SortMode {
+    int bs_nt, bs_vt;  // block sort
+    int nt, vt;        // merge passes (TMA-staged tiles)
+};
+#define MP_SORT_MODE_4 512, 33, 256, 33
+#define MP_SORT_MODE_4V 256, 33, 128, 33
+#define MP_SORT_MODE_8 256, 27, 128, 27
+#define MP_SORT_MODE_8V 256, 27, 128, 27
+#define MP_SORT_MODE_16 512, 4, 128, 8
 
-static int64_t block_tile(int key_bytes)
+static SortMode sort_mode(int key_bytes, bool vals)
 {
-    return (int64_t)BS_NT * (key_bytes == 16 ? BS_VT16 : (key_bytes == 8 ? BS_VT8 : BS_VT4));
+    if (key_bytes == 4) return vals ? SortMode{MP_SORT_MODE_4V} : SortMode{MP_SORT_MODE_4};
+    if (key_bytes == 8) return vals ? SortMode{MP_SORT_MODE_8V} : SortMode{MP_SORT_MODE_8};
+    return SortMode{MP_SORT_MODE_16};
 }
 
-static Shape sort_merge_shape(int key_bytes)
+static int64_t block_tile(int key_bytes, bool vals)
 {
-    // Tile of the merge passes: a power of two dividing 2 * block tile (a
-    // tile lies inside one run pair).  4-byte keys 256 x 16, 8-byte keys
-    // 128 x 16 (the same 2048-element tile as 256 x 8, merged faster),
-    // 16-byte keys 128 x 8.
-    Shape s;
-    s.nt = key_bytes == 4 ? 256 : 128;
-    s.vt = key_bytes == 16 ? 8 : 16;
-    s.staging = MP_STAGE_BULK;
-    return s;
+    const SortMode m = sort_mode(key_bytes, vals);
+    return (int64_t)m.bs_nt * m.bs_vt;
+}
+
+static Shape sort_merge_shape(int key_bytes, bool vals)
+{
+    const SortMode m = sort_mode(key_bytes, vals);
+    return Shape{m.nt, m.vt, MP_STAGE_BULK};
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -60,7 +74,7 @@ static int ceil_log2(int64_t x)
 size_t sort_workspace_bytes(const KeyKind& kind, int64_t n, bool with_values)
 {
     if (n <= 1) return 0;
-    const int64_t tiles = ceil_div(n, sort_merge_shape(kind.bytes).tile());
+    const int64_t tiles = ceil_div(n, sort_merge_shape(kind.bytes, with_values).tile());
     return align256((size_t)n * kind.bytes) + (with_values ? align256((size_t)n * 4) : 0) +
            align256((size_t)(tiles + 1) * 8);
 }
@@ -84,28 +98,27 @@ static cudaError_t launch_block_sort(const K* in, const uint32_t* vin, K* out, u
     return cudaGetLastError();
 }
 
+// Block-sort launch of one mode, its tile taken from the mode's macro.
+template <class K, bool VALS, int BNT, int BVT, int NT_, int VT_>
+static cudaError_t block_sort_mode(const void* in, const uint32_t* vin, void* out, uint32_t* vout,
+                                   int64_t n, const KeyKind& kind, cudaStream_t stream)
+{
+    return launch_block_sort<K, VALS, BNT, BVT>((const K*)in, vin, (K*)out, vout, n, kind, stream);
+}
+
 static cudaError_t block_sort(const KeyKind& kind, const void* in, const uint32_t* vin, void* out,
                               uint32_t* vout, int64_t n, cudaStream_t stream)
 {
     if (kind.bytes == 4) {
-        if (vin)
-            return launch_block_sort<uint32_t, true, BS_NT, BS_VT4>(
-                (const uint32_t*)in, vin, (uint32_t*)out, vout, n, kind, stream);
-        return launch_block_sort<uint32_t, false, BS_NT, BS_VT4>(
-            (const uint32_t*)in, nullptr, (uint32_t*)out, nullptr, n, kind, stream);
+        if (vin) return block_sort_mode<uint32_t, true, MP_SORT_MODE_4V>(in, vin, out, vout, n, kind, stream);
+        return block_sort_mode<uint32_t, false, MP_SORT_MODE_4>(in, nullptr, out, nullptr, n, kind, stream);
     }
     if (kind.bytes == 16) {
-        if (vin)
-            return launch_block_sort<u128, true, BS_NT, BS_VT16>((const u128*)in, vin, (u128*)out, vout, n, kind,
-                                                                 stream);
-        return launch_block_sort<u128, false, BS_NT, BS_VT16>((const u128*)in, nullptr, (u128*)out, nullptr, n,
-                                                              kind, stream);
+        if (vin) return block_sort_mode<u128, true, MP_SORT_MODE_16>(in, vin, out, vout, n, kind, stream);
+        return block_sort_mode<u128, false, MP_SORT_MODE_16>(in, nullptr, out, nullptr, n, kind, stream);
     }
-    if (vin)
-        return launch_block_sort<uint64_t, true, BS_NT, BS_VT8>(
-            (const uint64_t*)in, vin, (uint64_t*)out, vout, n, kind, stream);
-    return launch_block_sort<uint64_t, false, BS_NT, BS_VT8>(
-        (const uint64_t*)in, nullptr, (uint64_t*)out, nullptr, n, kind, stream);
+    if (vin) return block_sort_mode<uint64_t, true, MP_SORT_MODE_8V>(in, vin, out, vout, n, kind, stream);
+    return block_sort_mode<uint64_t, false, MP_SORT_MODE_8>(in, nullptr, out, nullptr, n, kind, stream);
 }
 
 mp_status sort_run(const KeyKind& kind, void* keys, uint32_t* vals, int64_t n, void* ws,
@@ -128,7 +141,9 @@ mp_status sort_run(const KeyKind& kind, void* keys, uint32_t* vals, int64_t n, v
     }
     int64_t* splits = reinterpret_cast<int64_t*>(w);
 
-    const int64_t bt = block_tile(kind.bytes);
+    const int64_t bt = block_tile(kind.bytes, with_vals);
+    const Shape ms = sort_merge_shape(kind.bytes, with_vals);
+    if ((2 * bt) % ms.tile() != 0) return fail(MP_ERR_INTERNAL, "sort: merge tile does not divide a run pair");
     const int passes = ceil_log2(ceil_div(n, bt));
     // The block sort writes where an even number of passes later ends in keys.
     void* cur = (passes & 1) ? ws_keys : keys;
@@ -139,7 +154,6 @@ mp_status sort_run(const KeyKind& kind, void* keys, uint32_t* vals, int64_t n, v
     cudaError_t e = block_sort(kind, keys, vals, cur, curv, n, stream);
     if (e != cudaSuccess) return cuda_fail(e, "block sort launch");
 
-    const Shape ms = sort_merge_shape(kind.bytes);
     for (int p = 0; p < passes; ++p) {
         MergeProblem mp;
         mp.kind = kind;

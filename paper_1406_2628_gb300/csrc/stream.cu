@@ -172,7 +172,7 @@ __device__ __forceinline__ int ring_search(const K* sA, uint32_t bA, int la, con
 template <class K, int VT, int CK, int C>
 __device__ __forceinline__ int ring_merge_indices(const K* sA, uint32_t bA, int la, const K* sB,
                                                   uint32_t bB, int lb, int ai, int bi, Codec<K> c,
-                                                  uint32_t (&packed)[VT / 2])
+                                                  uint32_t (&packed)[(VT + 1) / 2])
 {
     K ka = key_enc_ck<CK>(sA[wrap<C>(bA + ai)], c);
     K kb = key_enc_ck<CK>(sB[wrap<C>(bB + bi)], c);
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(NT) merge_stream_kernel(StreamArgs<K> p, unsig
         {
             const int diag = tid * VT < Lk ? tid * VT : Lk;
             const int ai = ring_search<CK, C>(skA, kbA, la, skB, kbB, lb, diag, p.codec);
-            uint32_t packed[VT / 2];
+            uint32_t packed[(VT + 1) / 2];
             const int ae = ring_merge_indices<K, VT, CK, C>(skA, kbA, la, skB, kbB, lb, ai, diag - ai, p.codec,
                                                             packed);
             put_indices<VT>(sidx, packed);

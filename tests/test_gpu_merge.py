@@ -19,6 +19,7 @@ SIZES = [(0, 0), (1, 0), (0, 1), (1, 1), (5, 3), (4095, 1), (4096, 4096), (12_30
 PLANS = [(128, 8), (256, 8), (128, 16), (256, 16), (512, 8),
          (128, 8, mp.MP_STAGE_BULK), (256, 8, mp.MP_STAGE_BULK), (128, 16, mp.MP_STAGE_BULK),
          (256, 16, mp.MP_STAGE_BULK), (128, 12, mp.MP_STAGE_BULK), (256, 12, mp.MP_STAGE_BULK),
+         (128, 27, mp.MP_STAGE_BULK), (128, 33, mp.MP_STAGE_BULK), (256, 33, mp.MP_STAGE_BULK),
          (128, 8, mp.MP_STAGE_WARP), (256, 8, mp.MP_STAGE_WARP), (128, 16, mp.MP_STAGE_WARP),
          (256, 16, mp.MP_STAGE_WARP)]
 

@@ -75,7 +75,8 @@ def test_sort_workload_scaled(order, dtype):
 
 BATCH_PLANS = [None, (128, 8), (256, 8), (128, 16), (256, 16),
                (128, 8, mp.MP_STAGE_VECTOR), (256, 16, mp.MP_STAGE_VECTOR),
-               (128, 16, mp.MP_STAGE_BULK), (256, 12, mp.MP_STAGE_BULK), (128, 12, mp.MP_STAGE_VECTOR)]
+               (128, 16, mp.MP_STAGE_BULK), (256, 12, mp.MP_STAGE_BULK), (128, 12, mp.MP_STAGE_VECTOR),
+               (128, 27, mp.MP_STAGE_BULK), (128, 33, mp.MP_STAGE_BULK)]
 
 
 def _batched_case(rng, nseg, max_len, dt=np.int32, empty_every=0):

@@ -14,7 +14,8 @@ from _util import first_mismatch, vals_to_dev
 pytestmark = pytest.mark.gpu
 
 KINDS = ["u128", "i128"]
-PLANS = [None, (128, 8, mp.MP_STAGE_BULK), (256, 8, mp.MP_STAGE_BULK), (128, 8, mp.MP_STAGE_STREAM),
+PLANS = [None, (128, 8, mp.MP_STAGE_BULK), (256, 8, mp.MP_STAGE_BULK), (128, 12, mp.MP_STAGE_BULK),
+         (128, 8, mp.MP_STAGE_STREAM),
          (256, 4, mp.MP_STAGE_STREAM)]
 
 
