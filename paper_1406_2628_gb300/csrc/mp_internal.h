@@ -153,9 +153,9 @@ mp_status check_merge_args_ext(const KeyKind& k, const void* a, const uint32_t* 
                                const uint32_t* outv, bool vals, const char* fn, int64_t out_n = -1);
 
 // Merge-based set operations (setops.cu): splits from launch_partition with
-// spacing setop_tile(key bytes); counts (uint32) and offsets (int64): one
-// per tile.
-int64_t setop_tile(int key_bytes);
+// spacing setop_tile(key bytes, values); counts (uint32) and offsets
+// (int64): one per tile.
+int64_t setop_tile(int key_bytes, bool vals);
 cudaError_t launch_setop(const MergeProblem& p, int op, const int64_t* splits, uint32_t* counts,
                          int64_t* offsets, int64_t cap, int64_t* count, cudaStream_t stream);
 
