@@ -589,6 +589,9 @@ static cudaError_t launch_setop_t(const MergeProblem& p, int op, const int64_t* 
     if (p.kind.identity())
         return launch_setop_ck<K, VALS, CODEC_IDENTITY>(p, op, splits, counts, offsets, block_sums, cap, count,
                                                         stream);
+    if (p.kind.signed_int())
+        return launch_setop_ck<K, VALS, CODEC_SIGNED>(p, op, splits, counts, offsets, block_sums, cap, count,
+                                                      stream);
     return launch_setop_ck<K, VALS, CODEC_RUNTIME>(p, op, splits, counts, offsets, block_sums, cap, count, stream);
 }
 
