@@ -77,8 +77,8 @@ typedef enum mp_dtype {
     MP_I64 = 4, /* int64_t  */
     /* Multi-word keys: 128-bit integers, two 64-bit words per key, the low
      * word first in memory (little-endian), 16-byte aligned.  Supported by
-     * the plain merges (tile plans MP_STAGE_BULK (128,8) / (256,8) / (128,12)
-     * and the streaming plans), mp_merge_path_partition, mp_sort, mp_set_operation
+     * the plain merges (tile plans MP_STAGE_BULK (128,8) / (256,8) / (128,12) /
+     * (128,9) and the streaming plans), mp_merge_path_partition, mp_sort, mp_set_operation
      * and mp_check_sorted; the batched, grouped, queued, checksum and
      * allocation-free entry points return MP_ERR_UNSUPPORTED_DTYPE. */
     MP_U128 = 5, /* unsigned 128-bit */

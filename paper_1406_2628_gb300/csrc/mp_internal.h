@@ -64,7 +64,7 @@ bool merge_shape_supported(int key_bytes, bool with_values, const Shape& shape);
 // The TMA-staged tile kernels (merge_bulk.cu): 4- and 8-byte keys in the
 // MP_BULK_SHAPES, 16-byte keys in the MP_WIDE_SHAPES (NT, VT).
 #define MP_BULK_SHAPES(X) X(128, 8) X(256, 8) X(128, 12) X(256, 12) X(128, 16) X(256, 16) X(128, 27) X(128, 33) X(256, 33)
-#define MP_WIDE_SHAPES(X) X(128, 8) X(256, 8) X(128, 12)
+#define MP_WIDE_SHAPES(X) X(128, 8) X(256, 8) X(128, 12) X(128, 9)
 cudaError_t launch_merge_bulk(const MergeProblem& p, const Shape& shape, const int64_t* a_split,
                               cudaStream_t stream);
 // Partition-free streaming merge (stream.cu): one launch, no scratch.

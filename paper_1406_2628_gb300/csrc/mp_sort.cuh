@@ -147,16 +147,25 @@ __device__ __forceinline__ void block_sort_body(const K* in, const uint32_t* vin
     register_sort<K, VALS, VT>(keys, tags);
 
     // 3. Merge rounds: runs of width w = VT * 2^r merge pairwise; the pair
-    //    of thread tid starts at run 2 * (tid >> (r + 1)).
+    //    of thread tid starts at run 2 * (tid >> (r + 1)).  While a pair's
+    //    2^(r+1) threads lie inside one warp (r < 5) its data is the warp's
+    //    own, and a warp barrier orders the writes and reads.
     for (int r = 0; (VT << r) < T; ++r) {
         const int w = VT << r;
-        __syncthreads();
+        const bool in_warp = (2 << r) <= 32;
+        if (in_warp)
+            __syncwarp();
+        else
+            __syncthreads();
 #pragma unroll
         for (int i = 0; i < VT; ++i) {
             sk[padded<K, PAD>(tid * VT + i)] = keys[i];
             if constexpr (VALS) stag[padded<uint16_t, PAD>(tid * VT + i)] = tags[i];
         }
-        __syncthreads();
+        if (in_warp)
+            __syncwarp();
+        else
+            __syncthreads();
         const int gs = ((tid >> (r + 1)) << (r + 1)) * VT;  // start of this thread's run pair
         const int diag = tid * VT - gs;
         // Diagonal search (Alg. 2) in the pair A = [gs, gs+w), B = [gs+w, gs+2w).
@@ -169,22 +178,50 @@ __device__ __forceinline__ void block_sort_body(const K* in, const uint32_t* vin
             else
                 lo = mid + 1;
         }
-        // Serial merge of VT outputs (ties take A).
-        int ai = lo, bi = diag - lo;
-        K ka = sk[padded<K, PAD>(gs + (ai < w ? ai : w - 1))];
-        K kb = sk[padded<K, PAD>(gs + w + (bi < w ? bi : w - 1))];
+        if constexpr (VALS) {
+            // Serial merge of VT outputs (ties take A), on absolute positions:
+            // A is [gs, gs + w), B is [gs + w, gs + 2w).  Each step reads the
+            // next element of the side it took, at most one past that side's
+            // end (B's start, the next pair's first element or the slack
+            // element at T), never used because the end tests come first;
+            // the tag follows the element taken.
+            int ai = gs + lo, bi = gs + w + diag - lo;
+            const int aend = gs + w, bend = gs + 2 * w;
+            K ka = sk[padded<K, PAD>(ai)];
+            K kb = sk[padded<K, PAD>(bi)];
 #pragma unroll
-        for (int i = 0; i < VT; ++i) {
-            const bool take_a = (bi >= w) || (ai < w && !(ka > kb));
-            keys[i] = take_a ? ka : kb;
-            if constexpr (VALS)
-                tags[i] = stag[padded<uint16_t, PAD>(take_a ? gs + ai : gs + w + bi)];
-            if (take_a) {
-                ++ai;
-                ka = sk[padded<K, PAD>(gs + (ai < w ? ai : w - 1))];
-            } else {
-                ++bi;
-                kb = sk[padded<K, PAD>(gs + w + (bi < w ? bi : w - 1))];
+            for (int i = 0; i < VT; ++i) {
+                const bool take_a = (bi >= bend) || (ai < aend && !(ka > kb));
+                const int src = take_a ? ai : bi;
+                keys[i] = take_a ? ka : kb;
+                tags[i] = stag[padded<uint16_t, PAD>(src)];
+                const int nxt = src + 1;
+                const K kn = sk[padded<K, PAD>(nxt)];
+                if (take_a) {
+                    ai = nxt;
+                    ka = kn;
+                } else {
+                    bi = nxt;
+                    kb = kn;
+                }
+            }
+        } else {
+            // Keys only: the same merge with the reads clamped into each run
+            // (measured faster here than the form above).
+            int ai = lo, bi = diag - lo;
+            K ka = sk[padded<K, PAD>(gs + (ai < w ? ai : w - 1))];
+            K kb = sk[padded<K, PAD>(gs + w + (bi < w ? bi : w - 1))];
+#pragma unroll
+            for (int i = 0; i < VT; ++i) {
+                const bool take_a = (bi >= w) || (ai < w && !(ka > kb));
+                keys[i] = take_a ? ka : kb;
+                if (take_a) {
+                    ++ai;
+                    ka = sk[padded<K, PAD>(gs + (ai < w ? ai : w - 1))];
+                } else {
+                    ++bi;
+                    kb = sk[padded<K, PAD>(gs + w + (bi < w ? bi : w - 1))];
+                }
             }
         }
     }
