@@ -67,10 +67,11 @@ def parse_args():
     p.add_argument("--plan", default=None, help="NT,VT tile plan (default: automatic)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the other workloads (plain keys, sort, batched, serving)")
-    p.add_argument("--extras", default="plain,sort,batched,serving,setops,wide,crossover",
+    p.add_argument("--extras", default="plain,sort,batched,serving,setops,wide,crossover,tiles",
                    help="comma list of extra workloads to run after the headline")
     p.add_argument("--serving-requests", type=int, default=50000)
     p.add_argument("--sort-log2-n", type=int, default=28, help="keys of the sort extra (log2)")
+    p.add_argument("--tiles-log2-n", type=int, default=27, help="keys per side of the tiles extra (log2)")
     p.add_argument("--batched-segments", type=int, default=16384, help="segments of the batched extra")
     return p.parse_args()
 
@@ -316,6 +317,47 @@ def extra_plain(mp, torch, dev, reps=50):
             "warm_us": warm_us, "cold_us": cold_us, "gkeys_s_warm": n / warm_us / 1e3,
             "gkeys_s_cold": n / cold_us / 1e3, "gbs_cold": 2 * n * 4 / cold_us / 1e3,
             "partitioned_cold_us": statistics.median(tcold)}
+
+
+def extra_tiles(mp, torch, dev, log2_n=27, reps=10):
+    """Keys-only merges of 2 x 2^log2_n keys through the TMA tile path at
+    several tile shapes (block threads, items per thread): uniform int32 and
+    int64 keys, and int32 runs with every A below every B (each tile then
+    comes from one side, the case where an even count per thread puts a
+    warp's serial walks into two banks).  Partition + merge per call."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(0x2628)
+    n = 1 << log2_n
+    e0, e1 = _events(torch)
+    res = {"n_a": n, "n_b": n}
+    bulk = mp.MP_STAGE_BULK
+    cases = [("i32_uniform", torch.int32, False, [(256, 16), (256, 12), (256, 33), (128, 33)]),
+             ("i32_a_below_b", torch.int32, True, [(256, 16), (256, 12), (256, 33), (128, 33)]),
+             ("i64_uniform", torch.int64, False, [(256, 12), (128, 16), (128, 27)])]
+    for name, dt, ordered, shapes in cases:
+        if ordered:
+            A = torch.arange(n, dtype=dt, device=dev)
+            B = torch.arange(n, 2 * n, dtype=dt, device=dev)
+        else:
+            hi = (1 << 31) - 1 if dt == torch.int32 else 1 << 62
+            A = torch.sort(torch.randint(-hi, hi, (n,), dtype=dt, device=dev, generator=g)).values
+            B = torch.sort(torch.randint(-hi, hi, (n,), dtype=dt, device=dev, generator=g)).values
+        out = torch.empty(2 * n, dtype=dt, device=dev)
+        row = {}
+        for nt, vt in shapes:
+            plan = (nt, vt, bulk)
+            for _ in range(3):
+                mp.mp_merge_plan(A, B, out_keys=out, plan=plan)
+            e0.record()
+            for _ in range(reps):
+                mp.mp_merge_plan(A, B, out_keys=out, plan=plan)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / reps
+            row[f"{nt}x{vt}"] = {"ms": ms, "gbs": 2 * 2 * n * A.element_size() / ms / 1e6}
+        res[name] = row
+        del A, B, out
+    return res
 
 
 def extra_crossover(mp, torch, dev, reps=15):
@@ -851,7 +893,8 @@ def run_ours(args):
                    "serving": lambda: extra_serving(mp, torch, dev, n_req=args.serving_requests),
                    "setops": lambda: extra_setops(mp, torch, dev),
                    "wide": lambda: extra_wide(mp, torch, dev),
-                   "crossover": lambda: extra_crossover(mp, torch, dev)}
+                   "crossover": lambda: extra_crossover(mp, torch, dev),
+                   "tiles": lambda: extra_tiles(mp, torch, dev, log2_n=args.tiles_log2_n)}
         del OK, OV
         for name in wanted:
             t0 = time.perf_counter()

@@ -74,8 +74,10 @@ __global__ void __launch_bounds__(256) grouped_partition_kernel(const GroupMerge
     asm volatile("griddepcontrol.launch_dependents;");
 }
 
-// One tile of problem p per CTA, windows staged by TMA bulk copies.
-template <class K, bool VALS, int NT, int VT>
+// One tile of problem p per CTA, windows staged by TMA bulk copies.  CK is
+// CODEC_IDENTITY when every problem of the launch has unsigned ascending
+// keys, else the runtime codec (each problem carries its own).
+template <class K, bool VALS, int NT, int VT, int CK>
 __global__ void __launch_bounds__(NT) grouped_merge_bulk_kernel(const GroupMergeDesc* descs,
                                                                 const int64_t* tile_first, int nprob,
                                                                 const int64_t* splits, unsigned int* err)
@@ -86,7 +88,7 @@ __global__ void __launch_bounds__(NT) grouped_merge_bulk_kernel(const GroupMerge
     const int p = problem_of(tile_first, nprob, tile);
     const TileArgs<K> a = tile_args_of<K>(descs[p]);
     const int64_t first = __ldg(tile_first + p);
-    merge_tile_bulk_body<K, VALS, NT, VT, CODEC_RUNTIME>(a, tile - first, splits + first + p, smem, err);
+    merge_tile_bulk_body<K, VALS, NT, VT, CK>(a, tile - first, splits + first + p, smem, err);
 }
 
 template <class K, bool VALS, int NT, int VT>
@@ -108,13 +110,13 @@ __global__ void __launch_bounds__(NT) grouped_block_sort_kernel(const GroupSortD
 // ---------------------------------------------------------------------------
 // Host side.
 // ---------------------------------------------------------------------------
-template <class K, bool VALS, int NT, int VT>
-static cudaError_t launch_grouped_merge_t(const GroupMergeDesc* d_descs, const int64_t* d_tile_first,
-                                          const int64_t* d_bound_first, int nprob,
-                                          int64_t total_tiles, int64_t* d_splits, cudaStream_t stream)
+template <class K, bool VALS, int NT, int VT, int CK>
+static cudaError_t launch_grouped_merge_ck(const GroupMergeDesc* d_descs, const int64_t* d_tile_first,
+                                           const int64_t* d_bound_first, int nprob,
+                                           int64_t total_tiles, int64_t* d_splits, cudaStream_t stream)
 {
     using SM = BulkSmem<K, VALS, NT, VT>;
-    auto kern = grouped_merge_bulk_kernel<K, VALS, NT, VT>;
+    auto kern = grouped_merge_bulk_kernel<K, VALS, NT, VT, CK>;
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
@@ -141,23 +143,35 @@ static cudaError_t launch_grouped_merge_t(const GroupMergeDesc* d_descs, const i
     return cudaLaunchKernelEx(&cfg, kern, d_descs, d_tile_first, nprob, (const int64_t*)d_splits, err);
 }
 
+template <class K, bool VALS, int NT, int VT>
+static cudaError_t launch_grouped_merge_t(const GroupMergeDesc* d_descs, const int64_t* d_tile_first,
+                                          const int64_t* d_bound_first, int nprob, int64_t total_tiles,
+                                          int64_t* d_splits, bool identity, cudaStream_t stream)
+{
+    if (identity)
+        return launch_grouped_merge_ck<K, VALS, NT, VT, CODEC_IDENTITY>(d_descs, d_tile_first, d_bound_first,
+                                                                        nprob, total_tiles, d_splits, stream);
+    return launch_grouped_merge_ck<K, VALS, NT, VT, CODEC_RUNTIME>(d_descs, d_tile_first, d_bound_first, nprob,
+                                                                   total_tiles, d_splits, stream);
+}
+
 // Grouped shapes: the default merge shapes of each key width.
 int64_t grouped_merge_tile(int key_bytes) { return key_bytes == 8 ? 256 * 8 : 256 * 16; }
 int64_t grouped_sort_tile(int key_bytes) { return key_bytes == 8 ? 256 * 8 : 256 * 16; }
 
 cudaError_t launch_grouped_merge(int key_bytes, bool vals, const GroupMergeDesc* d_descs,
                                  const int64_t* d_tile_first, const int64_t* d_bound_first,
-                                 int nprob, int64_t total_tiles, int64_t* d_splits,
+                                 int nprob, int64_t total_tiles, int64_t* d_splits, bool identity,
                                  cudaStream_t stream)
 {
     if (nprob <= 0) return cudaSuccess;
     // TMA-staged tiles: 4-byte keys 256 x 16 (tile 4096, = the block-sort
     // tile, so sort passes pair whole runs), 8-byte keys 256 x 8 (2048).
     if (key_bytes == 4)
-        return vals ? launch_grouped_merge_t<uint32_t, true, 256, 16>(d_descs, d_tile_first, d_bound_first, nprob, total_tiles, d_splits, stream)
-                    : launch_grouped_merge_t<uint32_t, false, 256, 16>(d_descs, d_tile_first, d_bound_first, nprob, total_tiles, d_splits, stream);
-    return vals ? launch_grouped_merge_t<uint64_t, true, 256, 8>(d_descs, d_tile_first, d_bound_first, nprob, total_tiles, d_splits, stream)
-                : launch_grouped_merge_t<uint64_t, false, 256, 8>(d_descs, d_tile_first, d_bound_first, nprob, total_tiles, d_splits, stream);
+        return vals ? launch_grouped_merge_t<uint32_t, true, 256, 16>(d_descs, d_tile_first, d_bound_first, nprob, total_tiles, d_splits, identity, stream)
+                    : launch_grouped_merge_t<uint32_t, false, 256, 16>(d_descs, d_tile_first, d_bound_first, nprob, total_tiles, d_splits, identity, stream);
+    return vals ? launch_grouped_merge_t<uint64_t, true, 256, 8>(d_descs, d_tile_first, d_bound_first, nprob, total_tiles, d_splits, identity, stream)
+                : launch_grouped_merge_t<uint64_t, false, 256, 8>(d_descs, d_tile_first, d_bound_first, nprob, total_tiles, d_splits, identity, stream);
 }
 
 template <class K, bool VALS, int NT, int VT>
@@ -206,6 +220,7 @@ extern "C" mp_status mp_merge_grouped(const mp_merge_desc* descs, int64_t nprob,
     std::vector<GroupMergeDesc> h(nprob);
     std::vector<int64_t> first(2 * nprob);
     int64_t tiles = 0;
+    bool all_identity = true;
     const int64_t T = grouped_merge_tile(k0.bytes);
     for (int64_t i = 0; i < nprob; ++i) {
         const mp_merge_desc& d = descs[i];
@@ -229,6 +244,7 @@ extern "C" mp_status mp_merge_grouped(const mp_merge_desc* descs, int64_t nprob,
         g.flip = k.flip;
         g.fmask = k.fmask;
         g.inv = k.inv;
+        all_identity = all_identity && k.identity();
         first[i] = tiles;
         first[nprob + i] = tiles + i;
         tiles += ceil_div(d.na + d.nb, T);
@@ -249,7 +265,7 @@ extern "C" mp_status mp_merge_grouped(const mp_merge_desc* descs, int64_t nprob,
     if (e == cudaSuccess)
         e = launch_grouped_merge(k0.bytes, vals, (const GroupMergeDesc*)d, (const int64_t*)(d + desc_bytes),
                                  (const int64_t*)(d + desc_bytes) + nprob, (int)nprob, tiles,
-                                 (int64_t*)(d + desc_bytes + first_bytes), s);
+                                 (int64_t*)(d + desc_bytes + first_bytes), all_identity, s);
     scratch_free(d, s);
     if (e != cudaSuccess) return cuda_fail(e, "mp_merge_grouped");
     return MP_OK;

@@ -137,9 +137,10 @@ struct GroupSortDesc {
 };
 // tile_first[p]: first tile of problem p (prefix of ceil(total/T));
 // bound_first[p] = tile_first[p] + p; d_splits: total_tiles + nprob int64.
+// identity: every problem has unsigned ascending keys (compiled codec).
 cudaError_t launch_grouped_merge(int key_bytes, bool vals, const GroupMergeDesc* d_descs,
                                  const int64_t* d_tile_first, const int64_t* d_bound_first,
-                                 int nprob, int64_t total_tiles, int64_t* d_splits,
+                                 int nprob, int64_t total_tiles, int64_t* d_splits, bool identity,
                                  cudaStream_t stream);
 cudaError_t launch_grouped_block_sort(int key_bytes, bool vals, const GroupSortDesc* d_descs,
                                       const int64_t* d_tile_first, int nprob, int64_t total_tiles,

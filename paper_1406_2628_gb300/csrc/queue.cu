@@ -387,9 +387,11 @@ static cudaError_t run_step(mp_queue* q, std::vector<Job*>& work, int slot, uint
                                           (const int64_t*)(dt + pl.off_first), pl.n, pl.tiles, q->s_compute);
             *launches += 1;
         } else {
+            bool identity = true;  // every problem of the launch has unsigned ascending keys
+            for (const GroupMergeDesc& d : g.m[pl.w][pl.v]) identity = identity && !d.flip && !d.fmask && !d.inv;
             e = launch_grouped_merge(kb, pl.v != 0, (const GroupMergeDesc*)(dt + pl.off_desc),
                                      (const int64_t*)(dt + pl.off_first), (const int64_t*)(dt + pl.off_first) + pl.n,
-                                     pl.n, pl.tiles, (int64_t*)(dt + pl.off_splits), q->s_compute);
+                                     pl.n, pl.tiles, (int64_t*)(dt + pl.off_splits), identity, q->s_compute);
             *launches += pl.tiles ? 2 : 1;
         }
         if (e != cudaSuccess) return e;
