@@ -23,13 +23,66 @@ __device__ unsigned int g_mp_kernel_error = 0;
 // ---------------------------------------------------------------------------
 // Partition: one thread per tile boundary, binary search along the diagonal
 // in global memory (Alg. 2; at most ceil(log2(min(|A|,|B|)+1)) probes, Thm 14).
+//
+// The search runs in two stages.  The split a(d) is the first a in
+// [lo, hi) with A[a] > B[d-1-a] (else hi), and that test is monotone in a,
+// so it can first be narrowed over the candidates a = jT only, then
+// finished inside the one interval ((j-1)T, jT] left.  With d = tT (every
+// tile boundary, also inside a sort pass's run pair) the first stage probes
+// A[jT] and B[(t-j)T - 1]: every T-th element of each side, a set shared by
+// all boundaries and held in L2, so only the second stage's probes (inside
+// one T-wide window per side) go to DRAM.  The result is the same split.
 // ---------------------------------------------------------------------------
+template <class FA, class FB>
+__device__ __forceinline__ int64_t diagonal_search_tiled(FA keyA, int64_t la, FB keyB, int64_t lb,
+                                                         int64_t diag, int64_t T)
+{
+    int64_t lo = diag - lb > 0 ? diag - lb : 0;
+    int64_t hi = diag < la ? diag : la;
+    if (lo < hi && T > 1) {
+        // Candidates jT in [lo, hi): j in [jlo, jhi].
+        const int64_t jlo = (lo + T - 1) / T, jhi = (hi - 1) / T;
+        int64_t a = jlo, b = jhi + 1;
+        while (a < b) {
+            const int64_t m = (a + b) >> 1;
+            if (keyA(m * T) > keyB(diag - 1 - m * T))
+                b = m;
+            else
+                a = m + 1;
+        }
+        // The test holds at aT (if a <= jhi) and fails at (a-1)T (if a > jlo).
+        if (a <= jhi) hi = a * T;
+        if (a > jlo) lo = (a - 1) * T + 1;
+    }
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (keyA(mid) > keyB(diag - 1 - mid))
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+template <class K>
+__device__ __forceinline__ int64_t partition_point_tiled(const TileArgs<K>& p, int64_t d, int64_t T)
+{
+    d = d < p.total ? d : p.total;
+    const Pair<K> q = pair_at(p, d < p.total ? d : p.total - 1);
+    const K* A = q.A;
+    const K* B = q.B;
+    const Codec<K> c = p.codec;
+    return diagonal_search_tiled([&](int64_t i) { return key_enc(ld_global_nc(A + i), c); }, q.na,
+                                 [&](int64_t i) { return key_enc(ld_global_nc(B + i), c); }, q.nb,
+                                 d - q.base, T);
+}
+
 template <class K>
 __global__ void __launch_bounds__(256) partition_kernel(TileArgs<K> p, int64_t spacing,
                                                         int64_t n_bounds, int64_t* a_split)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n_bounds) a_split[t] = partition_point(p, t * spacing);
+    if (t < n_bounds) a_split[t] = partition_point_tiled(p, t * spacing, spacing);
     // Let a dependent merge launch (programmatic dependent launch) start its
     // prologue; it waits on griddepcontrol.wait before reading a_split.
     asm volatile("griddepcontrol.launch_dependents;");
