@@ -30,16 +30,19 @@ __global__ void __launch_bounds__(NT) block_sort_kernel(const K* in, const uint3
 // number of outputs per thread the threads' runs start in different
 // shared-memory banks (in the block sort and in the passes).  4-byte keys
 // alone use 512 x 33 = 16,896-key blocks (2^28 keys need 14 passes, not the
-// 15 of 8192-key blocks); the modes with values, the 8-byte and the 16-byte
-// keys, whose threads hold more registers, sort 256-thread blocks (more CTAs
-// resident per SM), which measured faster than the larger blocks' saved
-// pass (16-byte keys: 256 x 9 blocks and 128 x 9 pass tiles, 2^25 keys in
-// 3.52 ms against 4.03 ms with 512 x 4 and 128 x 8).
+// 15 of 8192-key blocks) and 128 x 33 pass tiles (2^28 keys: 8.58 ms against
+// 8.80 ms with 256 x 33 tiles; 1024 x 33 blocks, one pass fewer, 8.89 ms:
+// the larger block sort costs more than the pass it saves); the modes with
+// values, the 8-byte and the 16-byte keys, whose threads hold more
+// registers, sort 256-thread blocks (more CTAs resident per SM), which
+// measured faster than the larger blocks' saved pass (16-byte keys: 256 x 9
+// blocks and 128 x 9 pass tiles, 2^25 keys in 3.52 ms against 4.03 ms with
+// 512 x 4 and 128 x 8).
 struct SortMode {
     int bs_nt, bs_vt;  // block sort
     int nt, vt;        // merge passes (TMA-staged tiles)
 };
-#define MP_SORT_MODE_4 512, 33, 256, 33
+#define MP_SORT_MODE_4 512, 33, 128, 33
 #define MP_SORT_MODE_4V 256, 33, 128, 33
 #define MP_SORT_MODE_8 256, 27, 128, 27
 #define MP_SORT_MODE_8V 256, 27, 128, 27

@@ -96,7 +96,7 @@ def test_graph_batched_replay():
 def test_resolve_plan_reports_the_shape_that_runs():
     big = 335_544_320
     assert mp.mp_merge_resolve_plan(torch.uint64, True, big) == (256, 12, mp.MP_STAGE_BULK)
-    assert mp.mp_merge_resolve_plan(torch.int32, False, big) == (256, 33, mp.MP_STAGE_BULK)
+    assert mp.mp_merge_resolve_plan(torch.int32, False, big) == (128, 33, mp.MP_STAGE_BULK)
     assert mp.mp_merge_resolve_plan(torch.int64, False, big) == (128, 27, mp.MP_STAGE_BULK)
     small = mp.mp_merge_resolve_plan(torch.int32, False, 1 << 20)
     assert small[2] == mp.MP_STAGE_STREAM
