@@ -115,7 +115,7 @@ static cudaError_t launch_grouped_merge_ck(const GroupMergeDesc* d_descs, const 
                                            const int64_t* d_bound_first, int nprob,
                                            int64_t total_tiles, int64_t* d_splits, cudaStream_t stream)
 {
-    using SM = BulkSmem<K, VALS, NT, VT>;
+    using SM = MergeBulkSmem<K, VALS, NT, VT>;
     auto kern = grouped_merge_bulk_kernel<K, VALS, NT, VT, CK>;
     static bool configured = false;
     if (!configured) {

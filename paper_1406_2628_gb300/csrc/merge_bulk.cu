@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(NT) merge_tile_bulk_kernel(TileArgs<K> p, unsi
 template <class K, bool VALS, int NT, int VT, int CK>
 static cudaError_t launch_bulk_ck(const MergeProblem& p, const int64_t* a_split, cudaStream_t stream)
 {
-    using SM = BulkSmem<K, VALS, NT, VT>;
+    using SM = MergeBulkSmem<K, VALS, NT, VT>;
     auto kern = merge_tile_bulk_kernel<K, VALS, NT, VT, CK>;
     static bool configured = false;  // attribute is per function, set once
     if (!configured) {

@@ -168,18 +168,20 @@ __device__ __forceinline__ EdgeLoad<E> edge_load(int j, const E* gA, int la, con
     return e;
 }
 
-template <class K, bool VALS, int NT, int VT>
+// Shared memory of a TMA-staged tile: keys, values (if VALS), the T source
+// indices (if IDX) and the mbarrier.
+template <class K, bool VALS, int NT, int VT, bool IDX = true>
 struct BulkSmem {
     static constexpr int T = NT * VT;
     static constexpr int EK = 16 / sizeof(K);
     static constexpr size_t keys_bytes = ((size_t)(T + 3 * EK) * sizeof(K) + 15) / 16 * 16;
     static constexpr size_t vals_bytes = VALS ? ((size_t)(T + 12) * 4 + 15) / 16 * 16 : 0;
-    static constexpr size_t idx_bytes = ((size_t)T * 2 + 15) / 16 * 16;
+    static constexpr size_t idx_bytes = IDX ? ((size_t)T * 2 + 15) / 16 * 16 : 0;
     static constexpr size_t bytes = keys_bytes + vals_bytes + idx_bytes + 16;  // + mbarrier
 };
 
-// Shared-memory regions of a TMA-staged tile.
-template <class K, bool VALS, int NT, int VT>
+// Shared-memory regions of a TMA-staged tile (sidx is null without IDX).
+template <class K, bool VALS, int NT, int VT, bool IDX = true>
 struct BulkLayout {
     K* sk;
     uint32_t* sv;
@@ -187,13 +189,26 @@ struct BulkLayout {
     uint64_t* bar;
     __device__ __forceinline__ explicit BulkLayout(unsigned char* smem)
     {
-        using SM = BulkSmem<K, VALS, NT, VT>;
+        using SM = BulkSmem<K, VALS, NT, VT, IDX>;
         sk = reinterpret_cast<K*>(smem);
         sv = reinterpret_cast<uint32_t*>(smem + SM::keys_bytes);
-        sidx = reinterpret_cast<uint16_t*>(smem + SM::keys_bytes + SM::vals_bytes);
+        sidx = IDX ? reinterpret_cast<uint16_t*>(smem + SM::keys_bytes + SM::vals_bytes) : nullptr;
         bar = reinterpret_cast<uint64_t*>(smem + SM::keys_bytes + SM::vals_bytes + SM::idx_bytes);
     }
 };
+
+// Merge tiles of 4-byte keys alone with an odd number of outputs per thread
+// keep the merged keys in registers and write them back over the windows
+// (merge_tile_bulk_body), so they need no source indices.
+template <class K, bool VALS, int VT>
+constexpr bool merge_keys_direct()
+{
+    return !VALS && sizeof(K) == 4 && (VT & 1) != 0;
+}
+
+// Shared memory of merge_tile_bulk_body's tile.
+template <class K, bool VALS, int NT, int VT>
+using MergeBulkSmem = BulkSmem<K, VALS, NT, VT, !merge_keys_direct<K, VALS, VT>()>;
 
 // Initialise the CTA's mbarrier (one thread); the caller then synchronises.
 __device__ __forceinline__ void bulk_init(uint64_t* bar)
@@ -254,23 +269,37 @@ __device__ __forceinline__ void merge_tile_bulk_body(const TileArgs<K>& p, int64
                                                      unsigned int* err)
 {
     constexpr int T = NT * VT;
+    constexpr bool DIRECT = merge_keys_direct<K, VALS, VT>();
     const int tid = threadIdx.x;
-    const BulkLayout<K, VALS, NT, VT> lay(smem);
+    const BulkLayout<K, VALS, NT, VT, !DIRECT> lay(smem);
     const TilePlace<K> t = tile_place(p, tile, T, a_split);
     const auto v = stage_view<K, VALS, NT, VT>(t, lay.sk, lay.sv, lay.sidx);
     bulk_init(lay.bar);
     __syncthreads();
     if (!bulk_stage<K, VALS, NT, VT>(t, v, lay.bar, 0, err)) return;
     const int L = t.la + t.lb;
-    {
-        const int diag = tid * VT < L ? tid * VT : L;
-        const int ai = smem_diagonal_search_ck<CK>(v.sA, t.la, v.sB, t.lb, diag, p.codec);
+    const int diag = tid * VT < L ? tid * VT : L;
+    const int ai = smem_diagonal_search_ck<CK>(v.sA, t.la, v.sB, t.lb, diag, p.codec);
+    if constexpr (DIRECT) {
+        // 4-byte keys alone, odd VT: the merged keys stay in registers and
+        // replace the windows in shared memory once every walk is done
+        // (thread-major writes at an odd stride touch 32 different banks),
+        // then leave with 128-bit loads and stores.  This skips the index
+        // stores and the gather of the general path.
+        K outk[VT];
+        serial_merge_keys_ck<K, VT, CK>(v.sA, t.la, v.sB, t.lb, ai, diag - ai, p.codec, outk);
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < VT; ++i) lay.sk[tid * VT + i] = outk[i];
+        __syncthreads();
+        store_linear<K, NT, VT>(lay.sk, L, p.out + t.d0);
+    } else {
         uint32_t packed[(VT + 1) / 2];
         serial_merge_indices_ck<K, VT, CK>(v.sA, t.la, v.sB, t.lb, ai, diag - ai, p.codec, packed);
         put_indices<VT>(lay.sidx, packed);
+        __syncthreads();
+        store_tile<K, VALS, NT, VT>(v, p.out + t.d0, VALS ? p.outv + t.d0 : nullptr);
     }
-    __syncthreads();
-    store_tile<K, VALS, NT, VT>(v, p.out + t.d0, VALS ? p.outv + t.d0 : nullptr);
 }
 
 // Order-sensitive fold of one merged output (key bits, value, position)

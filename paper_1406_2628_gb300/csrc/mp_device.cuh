@@ -112,6 +112,26 @@ __device__ __forceinline__ K key_dec(K e, Codec<K> c)
     return e ^ ((fill & c.fmask) | c.flip);
 }
 
+// Inverse of key_enc_ck.
+template <int CK, class K>
+__device__ __forceinline__ K key_dec_ck(K e, Codec<K> c)
+{
+    constexpr K top = (K)1 << (8 * sizeof(K) - 1);
+    if constexpr (CK == CODEC_IDENTITY) {
+        (void)c;
+        return e;
+    } else if constexpr (CK == CODEC_SIGNED) {
+        (void)c;
+        return e ^ top;
+    } else if constexpr (CK == CODEC_FLOAT) {
+        (void)c;
+        using S = signed_of<K>;
+        return e ^ ((K)((S)(~e) >> (8 * sizeof(K) - 1)) | top);
+    } else {
+        return key_dec(e, c);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // 128-bit global and shared memory access.
 // ---------------------------------------------------------------------------
@@ -370,6 +390,30 @@ __device__ __forceinline__ void serial_merge_indices_ck(const K* sA, int la, con
         if (take_a) { ka = kn; ++ai; }
         else { kb = kn; ++bi; }
     }
+}
+
+// The serial merge of serial_merge_indices_ck keeping the merged keys
+// themselves in registers instead of their sources (decoded back to their
+// stored form at the end): for tiles without values, whose outputs are then
+// written back to shared memory in thread order and stored linearly.  Same
+// reads, same decisions.
+template <class K, int VT, int CK>
+__device__ __forceinline__ void serial_merge_keys_ck(const K* sA, int la, const K* sB, int lb, int ai,
+                                                     int bi, Codec<K> c, K (&out)[VT])
+{
+    K ka = key_enc_ck<CK>(sA[ai], c);
+    K kb = key_enc_ck<CK>(sB[bi], c);
+#pragma unroll
+    for (int i = 0; i < VT; ++i) {
+        const bool take_a = (bi >= lb) || (ai < la && !(ka > kb));
+        out[i] = take_a ? ka : kb;
+        const K* nxt = take_a ? (sA + (ai < la ? ai + 1 : la)) : (sB + bi + 1);
+        const K kn = key_enc_ck<CK>(*nxt, c);
+        if (take_a) { ka = kn; ++ai; }
+        else { kb = kn; ++bi; }
+    }
+#pragma unroll
+    for (int i = 0; i < VT; ++i) out[i] = key_dec_ck<CK>(out[i], c);
 }
 
 // Serial merge on encoded keys carrying a 16-bit tag (block sort rounds).

@@ -250,6 +250,28 @@ __device__ __forceinline__ void store_tile(const TileView<K, VALS, NT, VT>& v, K
     }
 }
 
+// Write the tile's L outputs, held in order at so[0..L), to gout: 128-bit
+// shared loads and streaming stores when gout is 16-byte aligned.  so must
+// be 16-byte aligned.  Call after a __syncthreads() that follows the last
+// write of so.
+template <class K, int NT, int VT>
+__device__ __forceinline__ void store_linear(const K* so, int L, K* gout)
+{
+    constexpr int EK = 16 / sizeof(K);
+    const int tid = threadIdx.x;
+    if ((((uintptr_t)gout) & 15) == 0) {
+        const int nvec = L / EK;
+#pragma unroll
+        for (int j = 0; j < (VT + EK - 1) / EK; ++j) {
+            const int g = tid + j * NT;
+            if (g < nvec) st_global_cs_v4(gout + g * EK, *reinterpret_cast<const uint4*>(so + g * EK));
+        }
+        for (int j = nvec * EK + tid; j < L; j += NT) gout[j] = so[j];
+    } else {
+        for (int j = tid; j < L; j += NT) gout[j] = so[j];
+    }
+}
+
 // One tile of a merge problem (plain merge or sort pass): stage, split,
 // merge, store.  a_split holds the problem's split points at multiples of T.
 template <class K, bool VALS, int NT, int VT, int CK = CODEC_RUNTIME>
