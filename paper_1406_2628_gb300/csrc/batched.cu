@@ -118,24 +118,31 @@ __device__ __forceinline__ BatchTile batch_tile(const BatchArgs<K>& p, int64_t t
 // Per-thread part of a batched tile: find the thread's segment and its
 // split inside the staged window, merge VT outputs (stepping to the next
 // segment when both sides of the current one are used up) and record the
-// outputs' sources.
-template <class K, bool VALS, int NT, int VT, int CK>
-__device__ __forceinline__ void batched_thread_merge(const BatchArgs<K>& p, const BatchTile& bt,
-                                                     const TileView<K, VALS, NT, VT>& v)
+// outputs' sources in v.sidx, or (DIRECT) the merged keys themselves in
+// outk.  Returns false for a thread with no outputs in the tile.
+template <class K, bool VALS, int NT, int VT, int CK, bool DIRECT = false>
+__device__ __forceinline__ bool batched_thread_merge(const BatchArgs<K>& p, const BatchTile& bt,
+                                                     const TileView<K, VALS, NT, VT>& v,
+                                                     K* outk = nullptr)
 {
     const Codec<K> c = p.codec;
     const int tid = threadIdx.x;
     const int la = bt.la, lb = bt.lb, L = la + lb;
     const int64_t a0 = bt.a0, a1 = bt.a1, b0 = bt.b0, b1 = bt.b1;
     const int diag = tid * VT < L ? tid * VT : L;
-    if (diag >= L) return;
+    if (diag >= L) return false;
     uint32_t packed[(VT + 1) / 2];
     if (bt.s0 == bt.s1) {
         // The whole tile lies in one segment: a plain Merge Path tile.
         const int ai = smem_diagonal_search_ck<CK>(v.sA, la, v.sB, lb, diag, c);
-        serial_merge_indices_ck<K, VT, CK>(v.sA, la, v.sB, lb, ai, diag - ai, c, packed);
-        put_indices<VT>(v.sidx, packed);
-        return;
+        if constexpr (DIRECT) {
+            K (&ok)[VT] = *reinterpret_cast<K(*)[VT]>(outk);
+            serial_merge_keys_ck<K, VT, CK>(v.sA, la, v.sB, lb, ai, diag - ai, c, ok);
+        } else {
+            serial_merge_indices_ck<K, VT, CK>(v.sA, la, v.sB, lb, ai, diag - ai, c, packed);
+            put_indices<VT>(v.sidx, packed);
+        }
+        return true;
     }
     const int64_t dg = bt.d0 + diag;
     int64_t s = segment_of(p.a_off, p.b_off, bt.s0, bt.s1, dg);
@@ -172,6 +179,7 @@ __device__ __forceinline__ void batched_thread_merge(const BatchArgs<K>& p, cons
 #pragma unroll
     for (int i = 0; i < VT; ++i) {
         uint32_t src = 0;
+        K key = K(0);
         if (diag + i < L) {
             // Both sides of segment s used up: step to the next segment
             // (skipping empty ones); ai, bi already point at its first elements.
@@ -183,17 +191,23 @@ __device__ __forceinline__ void batched_thread_merge(const BatchArgs<K>& p, cons
             }
             const bool take_a = ai < aEnd && (bi >= bEnd || !(ka > kb));
             src = take_a ? (uint32_t)ai : (uint32_t)(la + bi);
+            key = take_a ? ka : kb;
             const K* nxt = take_a ? (v.sA + (ai < la ? ai + 1 : la)) : (v.sB + (bi < lb ? bi + 1 : lb));
             const K kn = key_enc_ck<CK>(*nxt, c);
             if (take_a) { ka = kn; ++ai; }
             else { kb = kn; ++bi; }
         }
-        if (i & 1)
-            packed[i / 2] |= src << 16;
-        else
-            packed[i / 2] = src;
+        if constexpr (DIRECT) {
+            outk[i] = key_dec_ck<CK>(key, c);
+        } else {
+            if (i & 1)
+                packed[i / 2] |= src << 16;
+            else
+                packed[i / 2] = src;
+        }
     }
-    put_indices<VT>(v.sidx, packed);
+    if constexpr (!DIRECT) put_indices<VT>(v.sidx, packed);
+    return true;
 }
 
 template <class K, bool VALS, int NT, int VT>
@@ -218,11 +232,13 @@ __global__ void __launch_bounds__(NT) batched_merge_kernel(BatchArgs<K> p)
 // Same, with the windows staged by TMA bulk copies (no staging registers),
 // compiled per key codec (CK).
 template <class K, bool VALS, int NT, int VT, int CK>
-__global__ void __launch_bounds__(NT) batched_merge_bulk_kernel(BatchArgs<K> p, unsigned int* err)
+__global__ void __launch_bounds__(NT, merge_keys_direct<K, VALS, VT>() ? 1024 / NT : 1)
+    batched_merge_bulk_kernel(BatchArgs<K> p, unsigned int* err)
 {
     constexpr int T = NT * VT;
+    constexpr bool DIRECT = merge_keys_direct<K, VALS, VT>();
     extern __shared__ __align__(16) unsigned char smem[];
-    const BulkLayout<K, VALS, NT, VT> lay(smem);
+    const BulkLayout<K, VALS, NT, VT, !DIRECT> lay(smem);
     bulk_init(lay.bar);
     __syncthreads();
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -240,9 +256,26 @@ __global__ void __launch_bounds__(NT) batched_merge_bulk_kernel(BatchArgs<K> p, 
         const auto v = stage_view<K, VALS, NT, VT>(t, lay.sk, lay.sv, lay.sidx);
         if (!bulk_stage<K, VALS, NT, VT>(t, v, lay.bar, parity, err)) return;
         parity ^= 1;
-        batched_thread_merge<K, VALS, NT, VT, CK>(p, bt, v);
-        __syncthreads();
-        store_tile<K, VALS, NT, VT>(v, p.out + bt.d0, VALS ? p.outv + bt.d0 : nullptr);
+        if constexpr (DIRECT) {
+            // As in merge_tile_bulk_body: the merged keys replace the
+            // windows in thread order and leave by 128-bit loads and stores.
+            K outk[VT];
+            const bool active = batched_thread_merge<K, VALS, NT, VT, CK, true>(p, bt, v, outk);
+            __syncthreads();
+            if (active) {
+#pragma unroll
+                for (int i = 0; i < VT; ++i) lay.sk[threadIdx.x * VT + i] = outk[i];
+            }
+            __syncthreads();
+            store_linear<K, NT, VT>(lay.sk, bt.la + bt.lb, p.out + bt.d0);
+            // Order these shared-memory accesses before the next tile's
+            // bulk copies into the same bytes.
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        } else {
+            batched_thread_merge<K, VALS, NT, VT, CK>(p, bt, v);
+            __syncthreads();
+            store_tile<K, VALS, NT, VT>(v, p.out + bt.d0, VALS ? p.outv + bt.d0 : nullptr);
+        }
         __syncthreads();
     }
 }
@@ -280,7 +313,7 @@ template <class K, bool VALS, int NT, int VT, bool BULK, int CK = CODEC_RUNTIME>
 static cudaError_t launch_batched_t(const BatchedProblem& q, int64_t* a_split, int64_t* seg_split,
                                     cudaStream_t stream)
 {
-    using SM = typename std::conditional<BULK, BulkSmem<K, VALS, NT, VT>, TileSmem<K, VALS, NT, VT>>::type;
+    using SM = typename std::conditional<BULK, MergeBulkSmem<K, VALS, NT, VT>, TileSmem<K, VALS, NT, VT>>::type;
     void (*kern)(BatchArgs<K>, unsigned int*) = nullptr;
     void (*kern_v)(BatchArgs<K>) = nullptr;
     if constexpr (BULK)
