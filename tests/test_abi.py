@@ -150,3 +150,30 @@ def test_queue_argument_errors(lib):
     assert lib.mp_queue_destroy(None) == mp.MP_OK
     assert lib.mp_graph_launch(None, None) == mp.MP_ERR_INVALID_ARG
     assert lib.mp_graph_destroy(None) == mp.MP_OK
+
+
+def test_default_plans_on_host(lib, monkeypatch):
+    """The automatic plan of each key kind (a host-side choice, no CUDA call):
+    the streaming merge (Alg. 3) up to its size limit, TMA-staged tiles above
+    it; explicit plans are reported as given."""
+    monkeypatch.delenv("MP_TUNE_CACHE", raising=False)
+    mp.mp_tune_clear()
+    bulk, stream = mp.MP_STAGE_BULK, mp.MP_STAGE_STREAM
+    big = 335_544_320
+    assert mp.mp_merge_resolve_plan(mp.MP_U64, True, big) == (256, 12, bulk)
+    assert mp.mp_merge_resolve_plan(mp.MP_I32, False, big) == (128, 33, bulk)
+    assert mp.mp_merge_resolve_plan(mp.MP_F32, False, big) == (128, 33, bulk)
+    assert mp.mp_merge_resolve_plan(mp.MP_I64, False, big) == (128, 27, bulk)
+    assert mp.mp_merge_resolve_plan(mp.MP_U128, False, big) == (128, 12, bulk)
+    assert mp.mp_merge_tile_items(mp.MP_U64, True, big) == 256 * 12
+    assert mp.mp_merge_tile_items(mp.MP_U32, False, big) == 128 * 33
+    # Small merges: the partition-free streaming plan, up to 2^22 outputs
+    # for 4-byte keys alone and 3 * 2^20 otherwise.
+    assert mp.mp_merge_resolve_plan(mp.MP_I32, False, 1 << 22) == (256, 8, stream)
+    assert mp.mp_merge_resolve_plan(mp.MP_I32, False, (1 << 22) + 1) == (128, 33, bulk)
+    assert mp.mp_merge_resolve_plan(mp.MP_U64, True, 3 << 20) == (128, 8, stream)
+    assert mp.mp_merge_resolve_plan(mp.MP_U64, True, (3 << 20) + 1) == (256, 12, bulk)
+    # Tile queries never report a streaming shape: they size split arrays.
+    assert mp.mp_merge_tile_items(mp.MP_I32, False, 1 << 20) == 128 * 33
+    # An explicit plan wins.
+    assert mp.mp_merge_resolve_plan(mp.MP_U64, True, big, (128, 8, bulk)) == (128, 8, bulk)
