@@ -68,6 +68,15 @@ MUTATIONS = [
     ("set op: difference keeps B's leftovers",
      "const int keep_b_alone = (op == 0 || op == 3);",
      "const int keep_b_alone = (op == 0 || op == 2 || op == 3);"),
+    ("merge stops when either side runs out",
+     "while (i < na || j < nb) {",
+     "while (i < na && j < nb) {"),
+    ("sort stops one round early",
+     "for (int64_t w = 1; w < n; w *= 2) {",
+     "for (int64_t w = 1; 2 * w < n; w *= 2) {"),
+    ("sort drops the second run of a ragged tail",
+     "int64_t hi = lo + 2 * w < n ? lo + 2 * w : n;",
+     "int64_t hi = lo + 2 * w < n ? lo + 2 * w : mid;"),
 ]
 
 PINS = [
