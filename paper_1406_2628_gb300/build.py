@@ -30,13 +30,10 @@ def nvcc_path() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libmp.so")
 
 
-def _flags(debug: bool):
-    f = ["-std=c++17", "-O3", ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
-         "-Xcompiler", "-fvisibility=hidden", "-I", INCLUDE, "-I", CSRC,
-         "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]
-    if debug:
-        f += ["-DMP_DEBUG=1"]
-    return f
+def _flags():
+    return ["-std=c++17", "-O3", ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
+            "-Xcompiler", "-fvisibility=hidden", "-I", INCLUDE, "-I", CSRC,
+            "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]
 
 
 def _sources():
@@ -55,12 +52,12 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB_PATH
     nvcc = nvcc_path()
     os.makedirs(BUILD_DIR, exist_ok=True)
-    flags = _flags(debug)
+    flags = _flags()
 
     def compile_one(src):
         obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
