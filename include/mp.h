@@ -116,7 +116,9 @@ typedef struct mp_plan {
  * rejects it (it takes no split points). */
 #define MP_STAGE_STREAM 4
 
-/* Text for a status code (static storage, never NULL). */
+/* Status, error detail and key sizes: library utilities, with no
+ * counterpart in the paper.
+ * Text for a status code (static storage, never NULL). */
 MP_API const char* mp_status_string(mp_status status);
 
 /* Detail of the last error returned on the calling thread ("" if none). */
@@ -139,7 +141,9 @@ MP_API mp_status mp_merge_keys(mp_dtype dtype, const void* a, int64_t na,
                         const void* b, int64_t nb, void* out, mp_stream_t stream);
 
 /*
- * mp_merge_pairs -- as mp_merge_keys, moving a uint32 value with every key.
+ * mp_merge_pairs -- as mp_merge_keys, moving a uint32 value with every key
+ * (Alg. 1; the paper merges bare keys, and each value follows its key's
+ * move along the path).
  *   a_vals[i] travels with a_keys[i], b_vals[j] with b_keys[j].  Outputs
  *   out_keys / out_vals (na+nb each) must not overlap any input.
  */
@@ -162,7 +166,8 @@ MP_API mp_status mp_merge_path_partition(mp_dtype dtype, const void* a, int64_t 
 
 /*
  * mp_merge_plan -- mp_merge_keys / mp_merge_pairs with an explicit tile
- * plan (NULL = automatic).  An unsupported plan returns MP_ERR_INVALID_ARG;
+ * plan (NULL = automatic): Alg. 1 with a chosen segment length per CTA
+ * (equal segments, Cor. 7).  An unsupported plan returns MP_ERR_INVALID_ARG;
  * mp_plan_supported() lists the compiled shapes.  Values are merged when any
  * of a_vals, b_vals, out_vals is non-NULL; pass all three NULL to merge keys
  * only.
@@ -173,7 +178,8 @@ MP_API mp_status mp_merge_plan(mp_dtype dtype,
                         void* out_keys, uint32_t* out_vals,
                         const mp_plan* plan, mp_stream_t stream);
 
-/* 1 if (block_threads, items_per_thread, staging) is a compiled merge shape. */
+/* 1 if (block_threads, items_per_thread, staging) is a compiled merge shape
+ * (a library query; no counterpart in the paper). */
 MP_API int mp_plan_supported(const mp_plan* plan);
 
 /*
@@ -182,13 +188,15 @@ MP_API int mp_plan_supported(const mp_plan* plan);
  * zero fields: automatic, which consults the tuned table and may pick the
  * streaming plan for small merges).  Writes it to *resolved (staging never
  * MP_STAGE_AUTO).  MP_ERR_INVALID_ARG for an unsupported plan or a NULL
- * resolved; MP_ERR_UNSUPPORTED_DTYPE for an unknown dtype.
+ * resolved; MP_ERR_UNSUPPORTED_DTYPE for an unknown dtype.  (A library
+ * query: the paper fixes the segment length as (|A|+|B|)/p, Alg. 1.)
  */
 MP_API mp_status mp_merge_resolve_plan(mp_dtype dtype, int with_values, int64_t total, const mp_plan* plan,
                                        mp_plan* resolved);
 
 /*
- * mp_merge_tile_items -- the tile length T (outputs per CTA) that
+ * mp_merge_tile_items -- the tile length T (outputs per CTA; Alg. 1's
+ * per-core length (|A|+|B|)/p with p = the number of tiles) that
  * mp_merge_partitioned uses for this dtype, payload choice, total output
  * length and plan (NULL = automatic; the automatic choice here is always a
  * partitioned tile plan, while an automatic mp_merge_plan / mp_merge_keys
@@ -221,7 +229,9 @@ MP_API mp_status mp_merge_partitioned(mp_dtype dtype,
  *   pool, copies the inputs in, runs mp_merge_pairs on `stream`, copies the
  *   outputs back and waits for `stream`.  a_vals = b_vals = out_vals = NULL
  *   merges keys only.  MP_ERR_NO_MEMORY if the device cannot hold the
- *   inputs and outputs.
+ *   inputs and outputs.  The merge is Alg. 1; the paper's arrays sit in one
+ *   shared memory, so the copies and their pipelining have no counterpart
+ *   in it.
  */
 MP_API mp_status mp_merge_pairs_host(mp_dtype dtype,
                                      const void* a_keys, const uint32_t* a_vals, int64_t na,
@@ -270,7 +280,8 @@ typedef enum mp_setop {
     MP_SET_SYMMETRIC_DIFFERENCE = 3
 } mp_setop;
 
-/* Output capacity (elements) mp_set_operation needs: na + nb for union and
+/* Output capacity (elements) mp_set_operation needs for the set operations
+ * above (Sec. I): na + nb for union and
  * symmetric difference, min(na, nb) for intersection, na for difference;
  * -1 for an unknown op or a negative size. */
 MP_API int64_t mp_set_capacity(mp_setop op, int64_t na, int64_t nb);
@@ -298,7 +309,8 @@ MP_API mp_status mp_set_operation(mp_setop op, mp_dtype dtype,
 
 /*
  * mp_sort_workspace_bytes -- device workspace that mp_sort needs for n keys
- * (with_values != 0: plus uint32 values).  0 for n <= 1.
+ * (with_values != 0: plus uint32 values): the second buffer between which
+ * the merge rounds of Sec. III alternate, plus split points.  0 for n <= 1.
  */
 MP_API size_t mp_sort_workspace_bytes(mp_dtype dtype, int64_t n, int with_values);
 
@@ -338,7 +350,9 @@ MP_API mp_status mp_merge_batched(mp_dtype dtype,
                            const mp_plan* plan, mp_stream_t stream);
 
 /* ------------------------------------------------------------------------
- * Autotuning of tile shapes.
+ * Autotuning of tile shapes.  The paper fixes only that segments are equal
+ * (Cor. 7); choosing their length and the thread shape per problem size is
+ * this library's own and has no counterpart in the paper.
  * ------------------------------------------------------------------------ */
 
 /*
@@ -376,7 +390,9 @@ MP_API void mp_tune_clear(void);
  * CUDA graphs: capture a merge once, replay it with one launch.  The graph
  * bakes in every pointer and size given at creation (the caller keeps those
  * buffers alive and may change their contents between replays) and owns its
- * scratch, so a replay allocates nothing.
+ * scratch, so a replay allocates nothing.  A launch-overhead measure with
+ * no counterpart in the paper; the replayed work is Alg. 1 (or the batched
+ * merge) unchanged.
  * ------------------------------------------------------------------------ */
 typedef struct mp_graph mp_graph;
 
@@ -409,7 +425,8 @@ MP_API mp_status mp_graph_destroy(mp_graph* graph);
  * 2: a set operation's tile output would pass the capacity, which only
  * unsorted inputs cause; that tile wrote nothing).
  * 0 means no kernel reported a problem since the last reset.  reset != 0
- * clears the flags after reading them.
+ * clears the flags after reading them.  (Robustness of this library; no
+ * counterpart in the paper.)
  */
 MP_API mp_status mp_kernel_error(unsigned int* code, int reset);
 
@@ -468,8 +485,9 @@ MP_API mp_status mp_merge_grouped(const mp_merge_desc* descs, int64_t nprob, int
                                   mp_stream_t stream);
 
 /*
- * mp_check_sorted -- SYNCHRONOUS check that keys[0..n) is ascending and, for
- * MP_F32, free of NaN.  Returns MP_OK, MP_ERR_NOT_SORTED or MP_ERR_NAN
+ * mp_check_sorted -- SYNCHRONOUS check of the precondition of Sec. II.A
+ * (inputs sorted): that keys[0..n) is ascending and, for MP_F32, free of
+ * NaN.  Returns MP_OK, MP_ERR_NOT_SORTED or MP_ERR_NAN
  * (NaN wins if both).  Waits for `stream`.
  */
 MP_API mp_status mp_check_sorted(mp_dtype dtype, const void* keys, int64_t n, mp_stream_t stream);
@@ -541,7 +559,8 @@ typedef struct mp_queue_stats {
     uint64_t waiting, active, bytes_in_use;
 } mp_queue_stats;
 
-/* Monotonic host clock (seconds) used for the timestamps in mp_result. */
+/* Monotonic host clock (seconds) used for the timestamps in mp_result (part
+ * of the serving layer, which has no counterpart in the paper). */
 MP_API double mp_clock_seconds(void);
 
 /*
@@ -576,7 +595,7 @@ MP_API mp_status mp_queue_destroy(mp_queue* q);
 
 /*
  * mp_generate -- synthetic keys on the device (the generator behind
- * MP_SRC_GENERATE).  SplitMix64 (Steele, Lea, Flood 2014) as a counter-based
+ * MP_SRC_GENERATE; input generation, no counterpart in the paper).  SplitMix64 (Steele, Lea, Flood 2014) as a counter-based
  * generator: x_i = mix(seed ^ (stream_id * 0xD1B54A32D192ED03) +
  * (i + 1) * 0x9E3779B97F4A7C15).  sorted != 0: key_i = i * stride +
  * (x_i mod stride) with stride = floor(2^w / n) (strictly increasing);
