@@ -67,7 +67,7 @@ def parse_args():
     p.add_argument("--plan", default=None, help="NT,VT tile plan (default: automatic)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the other workloads (plain keys, sort, batched, serving)")
-    p.add_argument("--extras", default="plain,sort,batched,serving,setops,wide,crossover,tiles",
+    p.add_argument("--extras", default="dists,plain,sort,batched,serving,setops,wide,crossover,tiles",
                    help="comma list of extra workloads to run after the headline")
     p.add_argument("--serving-requests", type=int, default=50000)
     p.add_argument("--sort-log2-n", type=int, default=28, help="keys of the sort extra (log2)")
@@ -486,6 +486,78 @@ def extra_setops(mp, torch, dev, log2_universe=28, reps=5):
     return res
 
 
+def _fill_large_kv(torch, dev, dist, A, B, seed):
+    """Overwrite the resident key buffers A (n_a) and B (n_b) (uint64) with
+    the large key-value recipe's other distributions, drawn on the device
+    (payloads stay the global source indices):
+    a_gt_b: A uniform in [2^63, 2^64), B uniform in [0, 2^63), each sorted;
+    interleaved: output rank r dealt to B iff floor((r+1) n_b / n) >
+    floor(r n_b / n), key r * floor(2^64 / n);
+    distinct16: 16 random 64-bit values, each element a uniform choice."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    n_a, n_b = A.numel(), B.numel()
+    a64, b64 = A.view(torch.int64), B.view(torch.int64)
+    top = -(1 << 63)  # the top bit as an int64 bit pattern
+    if dist == "a_gt_b":
+        a64.copy_(torch.sort(torch.randint(0, (1 << 63) - 1, (n_a,), dtype=torch.int64, device=dev,
+                                           generator=g)).values | top)
+        b64.copy_(torch.sort(torch.randint(0, (1 << 63) - 1, (n_b,), dtype=torch.int64, device=dev,
+                                           generator=g)).values)
+    elif dist == "interleaved":
+        n = n_a + n_b
+        r = torch.arange(n, dtype=torch.int64, device=dev)
+        to_b = ((r + 1) * n_b) // n > (r * n_b) // n
+        keys = r * ((1 << 64) // n)  # wraps as uint64 bits
+        a64.copy_(keys[~to_b])
+        b64.copy_(keys[to_b])
+        del r, to_b, keys
+    elif dist == "distinct16":
+        vals = torch.randint(-(1 << 63), (1 << 63) - 1, (16,), dtype=torch.int64, device=dev, generator=g)
+        vals = torch.sort(vals ^ top).values ^ top  # ascending as uint64
+        for t, m in ((a64, n_a), (b64, n_b)):
+            idx = torch.sort(torch.randint(0, 16, (m,), dtype=torch.int64, device=dev, generator=g)).values
+            t.copy_(vals[idx])
+            del idx
+    else:
+        raise ValueError(dist)
+
+
+def extra_dists(mp, torch, dev, A, AV, B, BV, OK, OV, peak, reps=20):
+    """The large key-value merge under the other three key distributions of
+    its recipe, on the same resident buffers: the whole step (partition +
+    merge) and the merge kernel alone, CUDA events on the launching stream."""
+    n = A.numel() + B.numel()
+    alg = 2 * n * 12
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for i, dist in enumerate(("a_gt_b", "interleaved", "distinct16")):
+        _fill_large_kv(torch, dev, dist, A, B, 0x14062628 + i)
+        torch.cuda.synchronize(dev)
+        for _ in range(3):
+            mp.mp_merge_pairs(A, AV, B, BV, OK, OV)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        for _ in range(reps):
+            mp.mp_merge_pairs(A, AV, B, BV, OK, OV)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        step_ms = e0.elapsed_time(e1) / reps
+        tile = mp.mp_merge_tile_items(torch.uint64, True, n, None)
+        splits = mp.mp_merge_path_partition(A, B, tile)
+        torch.cuda.synchronize(dev)
+        e1.record(stream)
+        for _ in range(reps):
+            mp.mp_merge_partitioned(A, B, splits, AV, BV, OK, OV)
+        e2.record(stream)
+        torch.cuda.synchronize(dev)
+        merge_ms = e1.elapsed_time(e2) / reps
+        res[dist] = {"ms": step_ms, "gkeys_s": n / step_ms / 1e6, "kernel_ms": merge_ms,
+                     "kernel_gbs": alg / merge_ms / 1e6, "frac": alg / merge_ms / 1e6 / peak}
+        del splits
+    return res
+
+
 def _device_sort_input(torch, dev, dtype, order, n, seed):
     g = torch.Generator(device=dev)
     g.manual_seed(seed)
@@ -494,8 +566,15 @@ def _device_sort_input(torch, dev, dtype, order, n, seed):
     else:
         bits = torch.randint(-(1 << 31), 1 << 31, (n,), dtype=torch.int64, device=dev, generator=g).to(torch.int32)
         x = bits.view(torch.float32)
-        nan = torch.isnan(x)
-        x[nan] = 1.0  # NaN excluded from the key order
+        # NaN is excluded from the key order: redraw those bit patterns
+        # (uniform over the non-NaN ones) until none is left.
+        while True:
+            nan = torch.nonzero(torch.isnan(x)).flatten()
+            if nan.numel() == 0:
+                break
+            fresh = torch.randint(-(1 << 31), 1 << 31, (nan.numel(),), dtype=torch.int64, device=dev,
+                                  generator=g).to(torch.int32)
+            bits[nan] = fresh
     if order == "sorted":
         x = torch.sort(x).values
     elif order == "reverse":
@@ -559,16 +638,21 @@ def extra_batched(mp, torch, dev, n_seg=16384, log2_max=18.0, reps=5):
     AO, BO = torch.from_numpy(a_off).to(dev), torch.from_numpy(b_off).to(dev)
     n = A.numel() + B.numel()
     out = torch.empty(n, dtype=torch.int32, device=dev)
+    # Tile shape, items per thread and staging picked by the autotuner on
+    # this very problem (it times every compiled shape), then used below.
+    t0 = time.perf_counter()
+    tuned = mp.mp_autotune_batched(A, AO, B, BO, out=out, reps=3)
+    tune_s = time.perf_counter() - t0
     for _ in range(2):
-        mp.mp_merge_batched(A, AO, B, BO, out=out)
+        mp.mp_merge_batched(A, AO, B, BO, out=out, plan=tuned)
     e0, e1 = _events(torch)
     e0.record()
     for _ in range(reps):
-        mp.mp_merge_batched(A, AO, B, BO, out=out)
+        mp.mp_merge_batched(A, AO, B, BO, out=out, plan=tuned)
     e1.record()
     torch.cuda.synchronize(dev)
     batched_ms = e0.elapsed_time(e1) / reps
-    g = mp.mp_graph_batched_create(A, AO, B, BO, out)
+    g = mp.mp_graph_batched_create(A, AO, B, BO, out, plan=tuned)
     g.replay()
     e0.record()
     for _ in range(reps):
@@ -599,7 +683,9 @@ def extra_batched(mp, torch, dev, n_seg=16384, log2_max=18.0, reps=5):
     per_call_ms = e0.elapsed_time(e1)
     per_call_wall_ms = (time.perf_counter() - t0) * 1e3
     byt = 2 * n * 4
-    return {"segments": n_seg, "keys": n, "batched_ms": batched_ms, "graph_ms": graph_ms,
+    return {"segments": n_seg, "keys": n, "tuned_plan": {"block_threads": tuned[0], "items_per_thread": tuned[1],
+                                                         "staging": {1: "vector", 2: "bulk"}.get(tuned[2])},
+            "tune_s": tune_s, "batched_ms": batched_ms, "graph_ms": graph_ms,
             "grouped_ms": grouped_ms, "per_call_ms": per_call_ms, "per_call_wall_ms": per_call_wall_ms,
             "batched_gkeys_s": n / batched_ms / 1e6, "batched_gbs": byt / batched_ms / 1e6,
             "graph_gbs": byt / graph_ms / 1e6, "per_call_gbs": byt / per_call_ms / 1e6,
@@ -719,6 +805,66 @@ def extra_serving(mp, torch, dev, n_req=50000, budget=8 << 30, rhos=(0.5, 0.9)):
             "serial": {"p50_ms": float(np.percentile(slat, 50) * 1e3), "p99_ms": float(np.percentile(slat, 99) * 1e3),
                        "throughput_gitems_s": items / smake / 1e9, "makespan_s": smake}}
     return out
+
+
+# --------------------------------------------------------------------- digest
+
+def _r(x, digits=4):
+    """x rounded to a few significant digits (None stays None)."""
+    if x is None or not isinstance(x, (int, float)) or x == 0 or not math.isfinite(x):
+        return x
+    return round(x, max(0, digits - 1 - int(math.floor(math.log10(abs(x))))))
+
+
+def summarize(line):
+    """The headline and every extra, a few numbers each (ms, GB/s, fractions
+    of the measured peak, latencies), in well under 1.5 kB of JSON."""
+    ex = line.get("extras", {})
+    rf = line.get("roofline", {})
+    sm = {"merge": {"gkeys_s": _r(line["value"]), "ms": _r(line["ms_per_step"]), "frac": _r(rf.get("frac")),
+                    "e2e_gkeys_s": _r(line.get("e2e", {}).get("value")),
+                    "e2e_ms": _r(line.get("e2e", {}).get("ms_per_step"))}}
+    d = ex.get("dists", {})
+    if "uniform" in d:
+        sm["dists"] = {k: [_r(v["ms"]), _r(v["frac"], 3)] for k, v in d.items()
+                       if isinstance(v, dict) and "frac" in v}
+    p = ex.get("plain", {})
+    if "cold_us" in p:
+        sm["plain_us"] = {"cold": _r(p["cold_us"], 3), "warm": _r(p["warm_us"], 3)}
+    so = ex.get("sort", {})
+    if "i32_random" in so:
+        sm["sort_ms"] = {dt: [_r(so[f"{dt}_{o}"]["ms"]) for o in ("random", "sorted", "reverse", "distinct256")
+                              if f"{dt}_{o}" in so] for dt in ("i32", "f32")}
+    b = ex.get("batched", {})
+    if "batched_ms" in b:
+        tp = b.get("tuned_plan", {})
+        sm["batched"] = {"ms": _r(b["batched_ms"]), "gbs": _r(b["batched_gbs"]), "graph_ms": _r(b["graph_ms"]),
+                         "per_call_ms": _r(b["per_call_ms"]), "x": _r(b["speedup_batched_vs_per_call"], 3),
+                         "plan": f"{tp.get('block_threads')}x{tp.get('items_per_thread')}{tp.get('staging', '')[:1]}"}
+    sv = ex.get("serving", {})
+    if "capacity" in sv:
+        sm["serving"] = {"cap_req_s": _r(sv["capacity"]["req_s"], 3)}
+        for k, v in sv.items():
+            if k.startswith("rho_"):
+                q, se = v["queue"], v["serial"]
+                sm["serving"][k] = {"q": [_r(q["p50_ms"], 3), _r(q["p99_ms"], 3), _r(q["throughput_gitems_s"], 3)],
+                                    "serial": [_r(se["p50_ms"], 3), _r(se["p99_ms"], 3),
+                                               _r(se["throughput_gitems_s"], 3)],
+                                    "failed": q["failed"]}
+    st = ex.get("setops", {})
+    if "union" in st:
+        short = {"union": "union", "intersection": "inter", "difference": "diff",
+                 "symmetric_difference": "sym", "union_pairs": "union_kv"}
+        sm["setops_ms"] = {v: _r(st[k]["ms"]) for k, v in short.items() if k in st}
+    w = ex.get("wide", {})
+    if "merge_auto" in w:
+        sm["u128_ms"] = {"merge": _r(w["merge_auto"]["ms"]), "sort": _r(w["sort"]["ms"])}
+    ro = ex.get("readonly_merge", {})
+    if "ms" in ro:
+        sm["readonly_ms"] = _r(ro["ms"])
+    sm["legend"] = ("dists: [step ms, merge-kernel frac of peak]; sort_ms: random, sorted, reverse, "
+                    "256 values; serving q/serial: [p50 ms, p99 ms, Gitems/s]")
+    return sm
 
 
 # --------------------------------------------------------------------- ours
@@ -887,6 +1033,16 @@ def run_ours(args):
     if not args.no_extras:
         extras = {}
         wanted = [x for x in args.extras.split(",") if x]
+        if "dists" in wanted:
+            t0 = time.perf_counter()
+            try:
+                extras["dists"] = extra_dists(mp, torch, dev, A, AV, B, BV, OK, OV, peak)
+            except Exception as exc:  # an extra never breaks the headline line
+                extras["dists"] = {"error": f"{type(exc).__name__}: {exc}"}
+            extras["dists"]["wall_s"] = time.perf_counter() - t0
+            extras["dists"]["uniform"] = {"ms": ms, "gkeys_s": n / ms / 1e6, "kernel_ms": merge_ms,
+                                          "kernel_gbs": achieved, "frac": achieved / peak}
+            wanted.remove("dists")
         runners = {"plain": lambda: extra_plain(mp, torch, dev),
                    "sort": lambda: extra_sort(mp, torch, dev, n=1 << args.sort_log2_n),
                    "batched": lambda: extra_batched(mp, torch, dev, n_seg=args.batched_segments),
@@ -913,6 +1069,9 @@ def run_ours(args):
                                 "sample": f"the full workload merged {reps_o}x by the single-threaded "
                                           f"oracle ({secs:.1f} s)",
                                 "host_cpus": os.cpu_count()}
+    # Last key of the line: a compact digest of every workload, so that a
+    # reader keeping only the tail of the output still has all of them.
+    line["summary"] = summarize(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

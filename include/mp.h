@@ -431,6 +431,45 @@ MP_API mp_status mp_graph_destroy(mp_graph* graph);
 MP_API mp_status mp_kernel_error(unsigned int* code, int reset);
 
 /*
+ * mp_kernel_status -- waits for `stream`, then turns the flags of
+ * mp_kernel_error into a status: MP_ERR_TIMEOUT if flag 1 is set (a staged
+ * tile's bounded wait ran out, so some output was not written),
+ * MP_ERR_NOT_SORTED if flag 2 is set (a set operation met unsorted input),
+ * else MP_OK.  reset != 0 clears the flags it read.  The flags are shared by
+ * all streams of the device.  (Robustness of this library; no counterpart
+ * in the paper.)
+ */
+MP_API mp_status mp_kernel_status(mp_stream_t stream, int reset);
+
+/* Fault kinds of mp_inject_fault. */
+typedef enum mp_fault {
+    MP_FAULT_SCRATCH_ALLOC = 1, /* the next `count` scratch allocations from the
+                                   library's pool fail: the call returns
+                                   MP_ERR_NO_MEMORY before enqueuing anything */
+    MP_FAULT_QUEUE_STEP = 2,    /* the next `count` steps of any request queue
+                                   fail as a rejected launch would, without
+                                   launching: every request in such a step
+                                   finishes with MP_ERR_CUDA */
+    MP_FAULT_STAGE_WAIT = 3     /* count > 0: from now on the first mbarrier
+                                   wait of every TMA-staged merge tile gives up
+                                   without polling (its bounded drain wait still
+                                   lets the copies land), so the tile writes
+                                   nothing and flag 1 of mp_kernel_error is set;
+                                   count == 0 turns this off.  SYNCHRONOUS:
+                                   waits for the device. */
+} mp_fault;
+
+/*
+ * mp_inject_fault -- a test hook for the error paths: makes failures happen
+ * on the host (allocation, queue step) or makes a device wait run out on
+ * purpose, without faulting the GPU.  count >= 0 (0 cancels).  Global to
+ * the process (the stage-wait switch: to the current device).  Returns
+ * MP_ERR_INVALID_ARG for an unknown kind or a negative count.  (Robustness
+ * of this library; no counterpart in the paper.)
+ */
+MP_API mp_status mp_inject_fault(mp_fault kind, int64_t count);
+
+/*
  * mp_merge_noalloc -- the merge of mp_merge_plan (values move when any value
  * pointer is non-NULL) for callers that must not allocate device memory on
  * the call path: code running inside another runtime's memory arena that
@@ -439,13 +478,18 @@ MP_API mp_status mp_kernel_error(unsigned int* code, int reset);
  * this is a deployment variant of Alg. 1.
  *   It calls no cudaMalloc, cudaFree or allocating library routine: the
  *   split points live in a fixed 2 MiB array compiled into the library
- *   (262144 entries, tile of 4096 outputs, 256 threads x 16 items), which
+ *   (262144 entries, TMA-staged tiles of 4096 outputs, 256 threads x 16
+ *   items), which
  *   every GPU that loads the library holds until the process exits.
  *   na + nb may be at most 1073737728; larger sizes return
  *   MP_ERR_INVALID_ARG before anything is enqueued.
  *   The first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress, no allocation) with that device current; make
- *   that first call before any stream capture.
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.  Under CUDA's default lazy module loading
+ *   that lookup is also when the runtime loads the array's module and so
+ *   takes its 2 MiB of device memory: make the first call before another
+ *   runtime's arena reserves the device's memory (or set
+ *   CUDA_MODULE_LOADING=EAGER).  Later calls take no memory.
  *   All calls share the one array: calls whose work overlaps on the GPU
  *   (other streams, other host threads) race and must not be issued; calls
  *   on one stream are ordered.  No part of the array needs to start at zero

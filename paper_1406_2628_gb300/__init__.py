@@ -119,6 +119,8 @@ _SIGNATURES = {
     "mp_merge_grouped": ([ctypes.POINTER(mp_merge_desc), _I64, _I32, _P], _I32),
     "mp_clock_seconds": ([], ctypes.c_double),
     "mp_kernel_error": ([ctypes.POINTER(ctypes.c_uint), _I32], _I32),
+    "mp_kernel_status": ([_P, _I32], _I32),
+    "mp_inject_fault": ([_I32, _I64], _I32),
     "mp_merge_noalloc": ([_I32, _P, _P, _I64, _P, _P, _I64, _P, _P, _P], _I32),
     "mp_merge_checksum": ([_I32, _P, _P, _I64, _P, _P, _I64, _P, _P], _I32),
     "mp_autotune_merge": ([_I32, _P, _P, _I64, _P, _P, _I64, _P, _P, _I32, ctypes.POINTER(mp_plan), _P], _I32),
@@ -487,6 +489,22 @@ def mp_kernel_error(reset: bool = False) -> int:
     v = ctypes.c_uint()
     _check(lib().mp_kernel_error(ctypes.byref(v), 1 if reset else 0))
     return v.value
+
+
+def mp_kernel_status(reset: bool = False, stream=None) -> int:
+    """Waits for the stream; the kernel error flags as a status code
+    (MP_OK, MP_ERR_TIMEOUT, MP_ERR_NOT_SORTED), returned, not raised."""
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(lib().mp_kernel_status(s.cuda_stream, 1 if reset else 0))
+
+
+# mp_fault
+MP_FAULT_SCRATCH_ALLOC, MP_FAULT_QUEUE_STEP, MP_FAULT_STAGE_WAIT = 1, 2, 3
+
+
+def mp_inject_fault(kind: int, count: int) -> None:
+    """Test hook: the next `count` events of this kind fail (see mp.h)."""
+    _check(lib().mp_inject_fault(int(kind), int(count)))
 
 
 def mp_clock_seconds() -> float:

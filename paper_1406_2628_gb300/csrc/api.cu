@@ -1,5 +1,6 @@
 // api.cu -- the C ABI (include/mp.h): argument checks, scratch memory,
 // dispatch to the kernels, status strings and the sortedness check.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -77,11 +78,28 @@ static mp_status get_pool(cudaMemPool_t* pool)
     return MP_OK;
 }
 
+// Host-side fault injection (mp_inject_fault): how many more scratch
+// allocations and queue steps are to fail.
+static std::atomic<int64_t> g_fault_count[4];
+
+bool take_fault(int kind)
+{
+    if (kind <= 0 || kind >= 4) return false;
+    int64_t c = g_fault_count[kind].load();
+    while (c > 0)
+        if (g_fault_count[kind].compare_exchange_weak(c, c - 1)) return true;
+    return false;
+}
+
 mp_status scratch_alloc(void** ptr, size_t bytes, cudaStream_t stream)
 {
     cudaMemPool_t pool;
     mp_status st = get_pool(&pool);
     if (st != MP_OK) return st;
+    if (take_fault(MP_FAULT_SCRATCH_ALLOC)) {
+        *ptr = nullptr;
+        return cuda_fail(cudaErrorMemoryAllocation, "scratch allocation (injected fault)");
+    }
     cudaError_t e = cudaMallocFromPoolAsync(ptr, bytes < 256 ? 256 : bytes, pool, stream);
     if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
     return MP_OK;
@@ -702,6 +720,23 @@ mp_status mp_check_sorted(mp_dtype dtype, const void* keys, int64_t n, mp_stream
     if (host_flags & 2u) return fail(MP_ERR_NAN, "mp_check_sorted: NaN key");
     if (host_flags & 1u) return fail(MP_ERR_NOT_SORTED, "mp_check_sorted: keys out of order");
     return MP_OK;
+}
+
+
+mp_status mp_inject_fault(mp_fault kind, int64_t count)
+{
+    if (count < 0) return fail(MP_ERR_INVALID_ARG, "mp_inject_fault: negative count");
+    switch (kind) {
+    case MP_FAULT_SCRATCH_ALLOC:
+    case MP_FAULT_QUEUE_STEP:
+        g_fault_count[kind].store(count);
+        return MP_OK;
+    case MP_FAULT_STAGE_WAIT: {
+        cudaError_t e = set_stage_wait_fault(count > 0);
+        return e == cudaSuccess ? MP_OK : cuda_fail(e, "mp_inject_fault");
+    }
+    }
+    return fail(MP_ERR_INVALID_ARG, "mp_inject_fault: unknown fault kind");
 }
 
 }  // extern "C"

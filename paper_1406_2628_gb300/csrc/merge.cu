@@ -18,7 +18,9 @@
 
 namespace mp {
 
-__device__ unsigned int g_mp_kernel_error = 0;
+// Word 0: the kernel error flags (mp_kernel_error).  Word 1: the
+// staging-wait fault switch (mp_inject_fault, MP_FAULT_STAGE_WAIT).
+__device__ unsigned int g_mp_kernel_error[2] = {0, 0};
 
 // ---------------------------------------------------------------------------
 // Partition: one thread per tile boundary, binary search along the diagonal
@@ -148,6 +150,15 @@ unsigned int* kernel_error_word()
         addr[dev] = static_cast<unsigned int*>(p);
     }
     return addr[dev];
+}
+
+cudaError_t set_stage_wait_fault(bool on)
+{
+    const unsigned int v = on ? 1u : 0u;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMemcpyToSymbol(g_mp_kernel_error, &v, sizeof v, sizeof(unsigned int));
+    return e;
 }
 
 // ---------------------------------------------------------------------------
@@ -363,6 +374,28 @@ extern "C" mp_status mp_kernel_error(unsigned int* code, int reset)
     }
     if (e != cudaSuccess) return mp::cuda_fail(e, "mp_kernel_error");
     if (code) *code = v;
+    return MP_OK;
+}
+
+extern "C" mp_status mp_kernel_status(mp_stream_t stream, int reset)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned int v = 0;
+    cudaError_t e = cudaMemcpyFromSymbolAsync(&v, mp::g_mp_kernel_error, sizeof v, 0,
+                                              cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && reset && v) {
+        const unsigned int z = 0;
+        e = cudaMemcpyToSymbolAsync(mp::g_mp_kernel_error, &z, sizeof z, 0, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) return mp::cuda_fail(e, "mp_kernel_status");
+    if (v & MP_KERR_MBAR_TIMEOUT)
+        return mp::fail(MP_ERR_TIMEOUT, "mp_kernel_status: a kernel's bounded wait for its staged "
+                                        "tile ran out; that tile's output was not written");
+    if (v & 2u)
+        return mp::fail(MP_ERR_NOT_SORTED, "mp_kernel_status: a set operation's tile output "
+                                           "passed the capacity (inputs not sorted)");
     return MP_OK;
 }
 

@@ -224,7 +224,8 @@ __device__ __forceinline__ void bulk_init(uint64_t* bar)
 // edges, every thread waits (bounded) for the mbarrier phase `parity`, and
 // the block agrees on the outcome (the barrier also publishes the edges).
 // Returns false, after recording MP_KERR_MBAR_TIMEOUT and giving copies in
-// flight a bounded time to land, if the wait ran out.  The caller must have
+// flight a bounded time to land, if the wait ran out.  err points at the
+// kernel error word; err[1] is read as the fault switch described below.  The caller must have
 // synchronised since the shared memory was last read.
 template <class K, bool VALS, int NT, int VT>
 __device__ __forceinline__ bool bulk_stage(const TilePlace<K>& t, const TileView<K, VALS, NT, VT>& v,
@@ -254,7 +255,12 @@ __device__ __forceinline__ bool bulk_stage(const TilePlace<K>& t, const TileView
             if (e.dst >= 0) (e.in_b ? v.vB : v.vA)[e.dst] = e.val;
         }
     }
-    const bool ok = __syncthreads_and(mbar_wait_bounded(bar, parity, WAIT_LIMIT));
+    // err[1] is the staging-wait fault switch (a host-side test hook): when
+    // set, the first wait gives up without polling, which exercises the
+    // path below; the drain wait keeps its full bound, so the copies in
+    // flight still land before the CTA returns.
+    const uint32_t first_limit = __ldcg(err + 1) ? 0u : WAIT_LIMIT;
+    const bool ok = __syncthreads_and(mbar_wait_bounded(bar, parity, first_limit));
     if (!ok) {
         if (tid == 0) atomicOr(err, MP_KERR_MBAR_TIMEOUT);
         mbar_wait_bounded(bar, parity, WAIT_LIMIT);

@@ -168,7 +168,14 @@ cudaError_t launch_merge_checksum(const MergeProblem& p, const int64_t* a_split,
                                   cudaStream_t stream);
 
 // Device address of the word kernels set when a bounded wait runs out.
+// The word after it is the staging-wait fault switch (mp_inject_fault):
+// nonzero makes bulk_stage's first wait give up without polling.
 unsigned int* kernel_error_word();
+cudaError_t set_stage_wait_fault(bool on);
+
+// Host-side fault injection: true (and one fewer left) if the next event of
+// this mp_fault kind is to fail.
+bool take_fault(int kind);
 
 // Errors: record a detail for mp_last_error() and return the status.
 mp_status fail(mp_status st, const std::string& detail);

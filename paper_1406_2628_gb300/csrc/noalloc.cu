@@ -13,7 +13,11 @@
 // calls in one stream are ordered and safe.  Nothing in it needs to start
 // at zero: the partition kernel writes every entry that the merge kernel
 // then reads.  The array stays resident on every GPU that loads the library
-// until the process exits.
+// until the process exits.  The device memory behind it is taken when the
+// CUDA runtime loads this file's module on a device; under CUDA's default
+// lazy module loading that happens at the first call on each device (the
+// cudaGetSymbolAddress lookup below), so that first call is the one that
+// must come before an arena reserves the device's memory.
 #include <mutex>
 
 #include "mp_internal.h"
@@ -61,7 +65,9 @@ extern "C" mp_status mp_merge_noalloc(mp_dtype dtype, const void* a_keys, const 
                                       int64_t nb, void* out_keys, uint32_t* out_vals,
                                       mp_stream_t stream)
 {
-    if (na >= 0 && nb >= 0 && na + nb > kNoallocMaxTotal)
+    // Written so that no sum can overflow: negative sizes are left to
+    // merge_prepare's checks.
+    if (na >= 0 && nb >= 0 && (na > kNoallocMaxTotal || nb > kNoallocMaxTotal - na))
         return fail(MP_ERR_INVALID_ARG,
                     "mp_merge_noalloc: na + nb exceeds the fixed scratch limit of 1073737728 outputs");
     const int base = (int)dtype & 0xFF;
@@ -70,7 +76,7 @@ extern "C" mp_status mp_merge_noalloc(mp_dtype dtype, const void* a_keys, const 
     MergeProblem p;
     Shape s;
     const bool vals = a_vals || b_vals || out_vals;
-    const mp_plan plan{kNoallocThreads, kNoallocItems, MP_STAGE_VECTOR, 0};
+    const mp_plan plan{kNoallocThreads, kNoallocItems, MP_STAGE_BULK, 0};
     mp_status st = merge_prepare(dtype, a_keys, a_vals, na, b_keys, b_vals, nb, out_keys, out_vals,
                                  vals, &plan, "mp_merge_noalloc", &p, &s);
     if (st != MP_OK) return st;

@@ -289,6 +289,9 @@ static cudaError_t grow_tables(mp_queue* q, int slot, size_t bytes)
 // kernel launches.
 static cudaError_t run_step(mp_queue* q, std::vector<Job*>& work, int slot, uint64_t* launches)
 {
+    // An injected fault (mp_inject_fault) fails the step the way a rejected
+    // launch would, before anything is enqueued.
+    if (take_fault(MP_FAULT_QUEUE_STEP)) return cudaErrorInvalidConfiguration;
     StepGroups g;
     for (Job* j : work) {
         const int w = j->kind.bytes == 8 ? 1 : 0;
@@ -416,7 +419,12 @@ static void worker_main(mp_queue* q)
                 if (j->last_enqueued) {
                     cudaError_t qe = cudaEventQuery(j->done);
                     if (qe != cudaErrorNotReady) {
-                        finish_job_locked(q, j, qe == cudaSuccess ? MP_OK : cuda_fail(qe, "queue step"));
+                        // A status recorded when the job's step failed to
+                        // launch stands, although its done event completes.
+                        const mp_status st = j->status != MP_OK ? j->status
+                                             : qe == cudaSuccess ? MP_OK
+                                                                 : cuda_fail(qe, "queue step");
+                        finish_job_locked(q, j, st);
                         q->active[i] = q->active.back();
                         q->active.pop_back();
                         q->cv_done.notify_all();

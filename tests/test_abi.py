@@ -177,3 +177,15 @@ def test_default_plans_on_host(lib, monkeypatch):
     assert mp.mp_merge_tile_items(mp.MP_I32, False, 1 << 20) == 128 * 33
     # An explicit plan wins.
     assert mp.mp_merge_resolve_plan(mp.MP_U64, True, big, (128, 8, bulk)) == (128, 8, bulk)
+
+
+def test_inject_fault_rejects_bad_arguments(lib):
+    # Both checks return before any CUDA call.
+    assert lib.mp_inject_fault(99, 1) == mp.MP_ERR_INVALID_ARG
+    assert "unknown" in mp.mp_last_error()
+    assert lib.mp_inject_fault(mp.MP_FAULT_SCRATCH_ALLOC, -1) == mp.MP_ERR_INVALID_ARG
+    assert "negative" in mp.mp_last_error()
+    # Host-side counters: setting and cancelling needs no GPU.
+    assert lib.mp_inject_fault(mp.MP_FAULT_SCRATCH_ALLOC, 3) == mp.MP_OK
+    assert lib.mp_inject_fault(mp.MP_FAULT_SCRATCH_ALLOC, 0) == mp.MP_OK
+    assert lib.mp_inject_fault(mp.MP_FAULT_QUEUE_STEP, 0) == mp.MP_OK

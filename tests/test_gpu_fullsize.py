@@ -6,8 +6,9 @@ bench times (automatic plans, default stream).
   (bit-exact; the payload = source index shows stability);
 * plain keys, 2 x 2^20 int32: the whole output against the oracle;
 * batched, 16,384 segments with per-side lengths up to 2^18 (~7e8 keys):
-  a seeded sample of segments merged one by one by the oracle, plus the
-  sortedness of every segment's output;
+  the whole output against the oracle's per-segment merge;
+* an int32 merge of 2^31 + 4097 outputs (past every 32-bit offset): the
+  whole output and the split points past 2^31 against the oracle;
 * sort of 2^28 keys (int32 and float32, four orders): properties that hold
   at any size -- the output is ascending under the key order (float: -0.0
   before +0.0) and is a permutation of the input (same multiset of bit
@@ -44,22 +45,62 @@ def test_plain_keys_full_size():
     assert np.array_equal(out.cpu().numpy(), ek)
 
 
-def test_batched_full_size_sampled():
+def test_batched_full_size():
     a, a_off, b, b_off = gen.batched()
     assert a.size + b.size > 5e8
     out = mp.mp_merge_batched(to_dev(a), to_dev(a_off), to_dev(b), to_dev(b_off)).cpu().numpy()
-    rng = np.random.default_rng(99)
-    nseg = a_off.size - 1
-    for s in list(rng.choice(nseg, 200, replace=False)) + [0, nseg - 1]:
-        ek, _ = oracle.merge(a[a_off[s]:a_off[s + 1]], b[b_off[s]:b_off[s + 1]])
-        c0, c1 = a_off[s] + b_off[s], a_off[s + 1] + b_off[s + 1]
-        assert np.array_equal(out[c0:c1], ek), s
-    # Every segment's output is ascending (segment starts excluded).
-    c = a_off + b_off
-    ok = np.ones(out.size, dtype=bool)
-    ok[1:] = out[1:] >= out[:-1]
-    ok[c[1:-1]] = True
-    assert ok.all()
+    torch.cuda.empty_cache()
+    # Every one of the 16,384 segments against the oracle's per-segment merge.
+    ek, _ = oracle.merge_batched(a, a_off, b, b_off)
+    assert first_mismatch(out, ek) is None
+
+
+def _chunks_equal(x: np.ndarray, y: np.ndarray, chunk: int = 1 << 27):
+    """First index where x and y differ (bit patterns), or None."""
+    assert x.shape == y.shape
+    for i in range(0, x.size, chunk):
+        bad = np.flatnonzero(x[i:i + chunk] != y[i:i + chunk])
+        if bad.size:
+            return i + int(bad[0])
+    return None
+
+
+def _sorted_int32_with_ties(seed: int, n: int, start: int, max_gap: int) -> np.ndarray:
+    """n sorted int32 keys from start, gaps uniform in [0, max_gap) (gap 0 =
+    a tie), made sorted by construction (a running sum)."""
+    rng = np.random.default_rng(seed)
+    x = rng.integers(0, max_gap, n, dtype=np.int8).astype(np.int64)
+    np.cumsum(x, out=x)
+    x += start
+    assert x[-1] < 2**31
+    return x.astype(np.int32)
+
+
+def test_merge_above_2e31_outputs():
+    """int32 keys, |A| = |B| = 2^30, plus 4097 more in B: 2^31 + 4097
+    outputs, so every output offset, split point and tile index past 2^31
+    goes through the 64-bit paths (Thm 14 / Cor. 6 make the method
+    independent of n).  The whole output against the oracle's merge, and the
+    partition's split points at diagonals past 2^31 against the oracle's
+    Alg. 2."""
+    na, nb = 1 << 30, (1 << 30) + 4097
+    a = _sorted_int32_with_ties(31, na, -(1 << 30), 3)
+    b = _sorted_int32_with_ties(32, nb, -(1 << 30) + 1, 3)
+    A, B = to_dev(a), to_dev(b)
+    out = mp.mp_merge_keys(A, B)
+    spacing = mp.mp_merge_tile_items(torch.int32, False, na + nb)
+    splits = mp.mp_merge_path_partition(A, B, spacing).cpu().numpy()
+    got = out.cpu().numpy()
+    del A, B, out
+    torch.cuda.empty_cache()
+    ek, _ = oracle.merge(a, b)
+    assert _chunks_equal(got, ek) is None
+    del ek
+    # Tile boundaries past 2^31 from the partition kernel.
+    n_bounds = splits.size
+    for t in [n_bounds - 1, n_bounds - 2, (1 << 31) // spacing, (1 << 31) // spacing + 1]:
+        d = min(t * spacing, na + nb)
+        assert splits[t] == oracle.split(a, b, d)[0], t
 
 
 def _ascending_total_order(x: np.ndarray) -> bool:

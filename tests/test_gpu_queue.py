@@ -204,3 +204,55 @@ def test_queue_continuous_batching_overlaps_requests():
         st = q.stats()
     # 32 merges (1 stage each) + 32 sorts (1 + 6 stages each) = 256 stages.
     assert st["steps"] < 256
+
+
+@pytest.mark.slow
+def test_queue_serving_distribution_at_bench_sizes():
+    """About 200 generated requests from the serving recipe (70 % merges,
+    30 % sorts, uint32 keys + uint32 values, sizes log-uniform in
+    [2^10, 2^24]) plus three merges and three sorts of 2^22..2^24 per side,
+    all submitted at once under a 1 GiB budget so that large multi-pass
+    sorts advance step by step beside other requests.  Every result against
+    the generator's host restatement run through the oracle, and against the
+    same request run alone through the plain calls; the budget holds."""
+    budget = 1 << 30
+    rng = np.random.default_rng(0x5E7)
+    specs = []
+    for i in range(194):
+        is_sort = rng.random() < 0.3
+        na = int(np.floor(2.0 ** (10 + 14 * rng.random())))
+        nb = 0 if is_sort else int(np.floor(2.0 ** (10 + 14 * rng.random())))
+        specs.append(("sort" if is_sort else "merge", na, nb))
+    big = [("merge", 1 << 24, 1 << 22), ("sort", 1 << 24, 0), ("merge", 3 << 21, 1 << 24),
+           ("sort", (1 << 22) + 12345, 0), ("merge", 1 << 22, (1 << 23) + 1), ("sort", 3 << 22, 0)]
+    for j, s in enumerate(big):
+        specs.insert(20 + 30 * j, s)
+    with mp.Queue(budget_bytes=budget, max_active=64) as q:
+        ts = []
+        for i, (op, na, nb) in enumerate(specs):
+            n = na + nb
+            ok = torch.empty(n, dtype=torch.int32)
+            ov = torch.empty(n, dtype=torch.int32)
+            seed = 9000 + i
+            t = q.submit_generated(mp.MP_OP_MERGE if op == "merge" else mp.MP_OP_SORT, mp.MP_U32,
+                                   na, nb, seed=seed, with_values=True, out_keys=ok, out_vals=ov)
+            ts.append((t, op, na, nb, seed, ok, ov))
+        for t, op, na, nb, seed, ok, ov in ts:
+            assert q.wait(t, timeout_s=300).status == mp.MP_OK, (op, na, nb)
+            got_k, got_v = ok.numpy().view(np.uint32), ov.numpy().view(np.uint32)
+            if op == "merge":
+                a, av, b, bv = gen.serving_request("merge", na, nb, seed)
+                ek, ev = oracle.merge(a, b, av, bv)
+                alone_k, alone_v = mp.mp_merge_pairs(to_dev(a), vals_to_dev(av), to_dev(b), vals_to_dev(bv))
+            else:
+                k, v = gen.serving_request("sort", na, 0, seed)
+                ek, ev = oracle.sort(k, v)
+                alone_k, alone_v = to_dev(k), vals_to_dev(v)
+                mp.mp_sort(alone_k, alone_v)
+            assert first_mismatch(got_k, ek) is None, (op, na, nb)
+            assert first_mismatch(got_v, ev) is None, (op, na, nb)
+            assert first_mismatch(to_host(alone_k, np.uint32), got_k) is None, (op, na, nb)
+            assert first_mismatch(to_host(alone_v, np.uint32), got_v) is None, (op, na, nb)
+        st = q.stats()
+        assert st["completed"] == len(specs) and st["failed"] == 0
+        assert st["peak_bytes"] <= budget
