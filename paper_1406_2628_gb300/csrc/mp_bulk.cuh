@@ -304,7 +304,7 @@ __device__ __forceinline__ void merge_tile_bulk_body(const TileArgs<K>& p, int64
         serial_merge_indices_ck<K, VT, CK>(v.sA, t.la, v.sB, t.lb, ai, diag - ai, p.codec, packed);
         put_indices<VT>(lay.sidx, packed);
         __syncthreads();
-        store_tile<K, VALS, NT, VT>(v, p.out + t.d0, VALS ? p.outv + t.d0 : nullptr);
+        store_tile<K, VALS, NT, VT, CK>(v, p.out + t.d0, VALS ? p.outv + t.d0 : nullptr, p.codec);
     }
 }
 

@@ -81,12 +81,21 @@ __host__ __device__ inline Codec<K> make_codec(uint64_t flip, uint64_t fmask, ui
 // negatives) and the runtime flip/fmask/inv codec (descending order).  Each
 // fixed kind computes key_enc with its codec's constants folded in.
 enum { CODEC_IDENTITY = 0, CODEC_RUNTIME = 1, CODEC_SIGNED = 2, CODEC_FLOAT = 3 };
+// The same three codecs for keys that are already encoded (the merge sort
+// keeps its intermediate runs encoded): compared as they are, decoded with
+// the codec on output.
+enum { CODEC_ENCODED_SIGNED = 4, CODEC_ENCODED_FLOAT = 5, CODEC_ENCODED_RUNTIME = 6 };
+template <int CK>
+constexpr bool codec_encoded_input()
+{
+    return CK >= CODEC_ENCODED_SIGNED;
+}
 
 template <int CK, class K>
 __device__ __forceinline__ K key_enc_ck(K x, Codec<K> c)
 {
     constexpr K top = (K)1 << (8 * sizeof(K) - 1);
-    if constexpr (CK == CODEC_IDENTITY) {
+    if constexpr (CK == CODEC_IDENTITY || codec_encoded_input<CK>()) {
         (void)c;
         return x;
     } else if constexpr (CK == CODEC_SIGNED) {
@@ -112,7 +121,8 @@ __device__ __forceinline__ K key_dec(K e, Codec<K> c)
     return e ^ ((fill & c.fmask) | c.flip);
 }
 
-// Inverse of key_enc_ck.
+// Inverse of key_enc_ck (for encoded-input kinds: the decoding of their
+// codec, since those keys arrive encoded).
 template <int CK, class K>
 __device__ __forceinline__ K key_dec_ck(K e, Codec<K> c)
 {
@@ -120,16 +130,27 @@ __device__ __forceinline__ K key_dec_ck(K e, Codec<K> c)
     if constexpr (CK == CODEC_IDENTITY) {
         (void)c;
         return e;
-    } else if constexpr (CK == CODEC_SIGNED) {
+    } else if constexpr (CK == CODEC_SIGNED || CK == CODEC_ENCODED_SIGNED) {
         (void)c;
         return e ^ top;
-    } else if constexpr (CK == CODEC_FLOAT) {
+    } else if constexpr (CK == CODEC_FLOAT || CK == CODEC_ENCODED_FLOAT) {
         (void)c;
         using S = signed_of<K>;
         return e ^ ((K)((S)(~e) >> (8 * sizeof(K) - 1)) | top);
     } else {
         return key_dec(e, c);
     }
+}
+
+// A key as it leaves a tile whose outputs are gathered from the staged
+// input: unchanged, except for encoded-input kinds, which decode it.
+template <int CK, class K>
+__device__ __forceinline__ K key_out_ck(K x, Codec<K> c)
+{
+    if constexpr (codec_encoded_input<CK>())
+        return key_dec_ck<CK>(x, c);
+    else
+        return x;
 }
 
 // ---------------------------------------------------------------------------

@@ -9,7 +9,14 @@
 //   3. log2(NT) rounds of Merge Path inside shared memory: runs of width w
 //      merge pairwise, each thread producing VT outputs of its pair after a
 //      diagonal search (Alg. 2) in that pair;
-//   4. coalesced store (keys decoded; values gathered by source position).
+//   4. coalesced store (keys decoded, or left encoded for the merge passes
+//      that follow; values gathered by source position).
+// Without values each run pair is laid out bitonically: A ascending, then B
+// descending, so that a walk that runs past the end of A reads B's largest
+// key and one past the end of B reads A's largest.  Those act as sentinels:
+// the serial merge needs no end tests, and where a sentinel ties the other
+// side's head the key taken has the same value, which is all a keys-only
+// sort can observe.
 // With VT even, shared arrays are padded by one element per 128 bytes, so
 // the thread-major accesses (thread t touching elements t*VT .. t*VT+VT-1)
 // and the strided reads of the merge rounds spread over the banks; with VT
@@ -106,9 +113,53 @@ __device__ __forceinline__ void register_sort(K (&k)[VT], uint16_t (&g)[VT])
     for (int c = 0; c < BatcherNet<VT>::N; ++c) cmp_swap<K, VALS, VT>(k, g, net.a[c], net.b[c]);
 }
 
+// Keys-only merge round in the bitonic layout.  Thread tid's VT sorted keys
+// belong to run tid >> r (runs of w = VT << r); threads of odd runs (the B
+// side of their pair) store their block mirrored, so B reads descending.
+template <class K, bool PAD, int VT>
+__device__ __forceinline__ void bitonic_round_store(K* sk, int tid, int r, const K (&keys)[VT])
+{
+    const int w = VT << r;
+    const bool is_b = (tid >> r) & 1;
+    const int gs = ((tid >> (r + 1)) << (r + 1)) * VT;
+    const int s = is_b ? gs + 2 * w - ((tid & ((1 << r) - 1)) + 1) * VT : tid * VT;
+#pragma unroll
+    for (int i = 0; i < VT; ++i) sk[padded<K, PAD>(s + i)] = is_b ? keys[VT - 1 - i] : keys[i];
+}
+
+// Diagonal search (Alg. 2) and serial merge of VT outputs in a bitonic run
+// pair at gs: A[i] at gs + i, B[j] at gs + 2w - 1 - j.
+template <class K, bool PAD, int VT>
+__device__ __forceinline__ void bitonic_round_merge(const K* sk, int gs, int w, int diag, K (&keys)[VT])
+{
+    int lo = diag - w > 0 ? diag - w : 0;
+    int hi = diag < w ? diag : w;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        // A[mid] against B[diag - 1 - mid]
+        if (sk[padded<K, PAD>(gs + mid)] > sk[padded<K, PAD>(gs + 2 * w - diag + mid)])
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    int pa = gs + lo, pb = gs + 2 * w - 1 - (diag - lo);
+    K ka = sk[padded<K, PAD>(pa)], kb = sk[padded<K, PAD>(pb)];
+#pragma unroll
+    for (int i = 0; i < VT; ++i) {
+        const bool take_a = !(ka > kb);  // ties take A
+        keys[i] = take_a ? ka : kb;
+        pa += take_a ? 1 : 0;
+        pb -= take_a ? 0 : 1;
+        const K nv = sk[padded<K, PAD>(take_a ? pa : pb)];
+        ka = take_a ? nv : ka;
+        kb = take_a ? kb : nv;
+    }
+}
+
 // Sorts tile `tile` of in[0..n) into out (out may equal in: a CTA reads its
-// whole tile before writing).
-template <class K, bool VALS, int NT, int VT>
+// whole tile before writing).  ENC_OUT leaves the keys encoded (unsigned
+// order) for merge passes that compare them as they are.
+template <class K, bool VALS, int NT, int VT, bool ENC_OUT = false>
 __device__ __forceinline__ void block_sort_body(const K* in, const uint32_t* vin, K* out,
                                                 uint32_t* vout, int64_t n, Codec<K> c, int64_t tile,
                                                 unsigned char* smem)
@@ -150,77 +201,78 @@ __device__ __forceinline__ void block_sort_body(const K* in, const uint32_t* vin
     //    of thread tid starts at run 2 * (tid >> (r + 1)).  While a pair's
     //    2^(r+1) threads lie inside one warp (r < 5) its data is the warp's
     //    own, and a warp barrier orders the writes and reads.
-    for (int r = 0; (VT << r) < T; ++r) {
-        const int w = VT << r;
-        const bool in_warp = (2 << r) <= 32;
-        if (in_warp)
-            __syncwarp();
-        else
-            __syncthreads();
-#pragma unroll
-        for (int i = 0; i < VT; ++i) {
-            sk[padded<K, PAD>(tid * VT + i)] = keys[i];
-            if constexpr (VALS) stag[padded<uint16_t, PAD>(tid * VT + i)] = tags[i];
-        }
-        if (in_warp)
-            __syncwarp();
-        else
-            __syncthreads();
-        const int gs = ((tid >> (r + 1)) << (r + 1)) * VT;  // start of this thread's run pair
-        const int diag = tid * VT - gs;
-        // Diagonal search (Alg. 2) in the pair A = [gs, gs+w), B = [gs+w, gs+2w).
-        int lo = diag - w > 0 ? diag - w : 0;
-        int hi = diag < w ? diag : w;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (sk[padded<K, PAD>(gs + mid)] > sk[padded<K, PAD>(gs + w + diag - 1 - mid)])
-                hi = mid;
+    if constexpr (!VALS) {
+        // Merge rounds on the bitonic layout (the pair of thread tid starts
+        // at run 2 * (tid >> (r + 1)); warp barriers while it lies in one warp).
+        for (int r = 0; (VT << r) < T; ++r) {
+            const bool in_warp = (2 << r) <= 32;
+            if (in_warp)
+                __syncwarp();
             else
-                lo = mid + 1;
+                __syncthreads();
+            bitonic_round_store<K, PAD, VT>(sk, tid, r, keys);
+            if (in_warp)
+                __syncwarp();
+            else
+                __syncthreads();
+            const int gs = ((tid >> (r + 1)) << (r + 1)) * VT;
+            bitonic_round_merge<K, PAD, VT>(sk, gs, VT << r, tid * VT - gs, keys);
         }
-        if constexpr (VALS) {
-            // Serial merge of VT outputs (ties take A), on absolute positions:
-            // A is [gs, gs + w), B is [gs + w, gs + 2w).  Each step reads the
-            // next element of the side it took, at most one past that side's
-            // end (B's start, the next pair's first element or the slack
-            // element at T), never used because the end tests come first;
-            // the tag follows the element taken.
-            int ai = gs + lo, bi = gs + w + diag - lo;
-            const int aend = gs + w, bend = gs + 2 * w;
-            K ka = sk[padded<K, PAD>(ai)];
-            K kb = sk[padded<K, PAD>(bi)];
+    } else {
+        for (int r = 0; (VT << r) < T; ++r) {
+            const int w = VT << r;
+            const bool in_warp = (2 << r) <= 32;
+            if (in_warp)
+                __syncwarp();
+            else
+                __syncthreads();
 #pragma unroll
             for (int i = 0; i < VT; ++i) {
-                const bool take_a = (bi >= bend) || (ai < aend && !(ka > kb));
-                const int src = take_a ? ai : bi;
-                keys[i] = take_a ? ka : kb;
-                tags[i] = stag[padded<uint16_t, PAD>(src)];
-                const int nxt = src + 1;
-                const K kn = sk[padded<K, PAD>(nxt)];
-                if (take_a) {
-                    ai = nxt;
-                    ka = kn;
-                } else {
-                    bi = nxt;
-                    kb = kn;
-                }
+                sk[padded<K, PAD>(tid * VT + i)] = keys[i];
+                stag[padded<uint16_t, PAD>(tid * VT + i)] = tags[i];
             }
-        } else {
-            // Keys only: the same merge with the reads clamped into each run
-            // (measured faster here than the form above).
-            int ai = lo, bi = diag - lo;
-            K ka = sk[padded<K, PAD>(gs + (ai < w ? ai : w - 1))];
-            K kb = sk[padded<K, PAD>(gs + w + (bi < w ? bi : w - 1))];
+            if (in_warp)
+                __syncwarp();
+            else
+                __syncthreads();
+            const int gs = ((tid >> (r + 1)) << (r + 1)) * VT;  // start of this thread's run pair
+            const int diag = tid * VT - gs;
+            // Diagonal search (Alg. 2) in the pair A = [gs, gs+w), B = [gs+w, gs+2w).
+            int lo = diag - w > 0 ? diag - w : 0;
+            int hi = diag < w ? diag : w;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (sk[padded<K, PAD>(gs + mid)] > sk[padded<K, PAD>(gs + w + diag - 1 - mid)])
+                    hi = mid;
+                else
+                    lo = mid + 1;
+            }
+            {
+                // Serial merge of VT outputs (ties take A), on absolute positions:
+                // A is [gs, gs + w), B is [gs + w, gs + 2w).  Each step reads the
+                // next element of the side it took, at most one past that side's
+                // end (B's start, the next pair's first element or the slack
+                // element at T), never used because the end tests come first;
+                // the tag follows the element taken.
+                int ai = gs + lo, bi = gs + w + diag - lo;
+                const int aend = gs + w, bend = gs + 2 * w;
+                K ka = sk[padded<K, PAD>(ai)];
+                K kb = sk[padded<K, PAD>(bi)];
 #pragma unroll
-            for (int i = 0; i < VT; ++i) {
-                const bool take_a = (bi >= w) || (ai < w && !(ka > kb));
-                keys[i] = take_a ? ka : kb;
-                if (take_a) {
-                    ++ai;
-                    ka = sk[padded<K, PAD>(gs + (ai < w ? ai : w - 1))];
-                } else {
-                    ++bi;
-                    kb = sk[padded<K, PAD>(gs + w + (bi < w ? bi : w - 1))];
+                for (int i = 0; i < VT; ++i) {
+                    const bool take_a = (bi >= bend) || (ai < aend && !(ka > kb));
+                    const int src = take_a ? ai : bi;
+                    keys[i] = take_a ? ka : kb;
+                    tags[i] = stag[padded<uint16_t, PAD>(src)];
+                    const int nxt = src + 1;
+                    const K kn = sk[padded<K, PAD>(nxt)];
+                    if (take_a) {
+                        ai = nxt;
+                        ka = kn;
+                    } else {
+                        bi = nxt;
+                        kb = kn;
+                    }
                 }
             }
         }
@@ -235,7 +287,7 @@ __device__ __forceinline__ void block_sort_body(const K* in, const uint32_t* vin
     // 4. Coalesced store.
 #pragma unroll 4
     for (int j = tid; j < L; j += NT) {
-        out[base + j] = key_dec(sk[padded<K, PAD>(j)], c);
+        out[base + j] = ENC_OUT ? sk[padded<K, PAD>(j)] : key_dec(sk[padded<K, PAD>(j)], c);
         if constexpr (VALS) vout[base + j] = sv[stag[padded<uint16_t, PAD>(j)]];
     }
 }

@@ -182,9 +182,10 @@ __device__ __forceinline__ void put_indices(uint16_t* sidx, const uint32_t (&pac
 
 // Gather by source index and write the tile's L outputs to gout (and gvout).
 // Call after a __syncthreads() that follows every put_indices().
-template <class K, bool VALS, int NT, int VT>
+// Encoded-input codec kinds (CK) decode each key on the way out.
+template <class K, bool VALS, int NT, int VT, int CK = CODEC_IDENTITY>
 __device__ __forceinline__ void store_tile(const TileView<K, VALS, NT, VT>& v, K* gout,
-                                           uint32_t* gvout)
+                                           uint32_t* gvout, Codec<K> c = Codec<K>{})
 {
     constexpr int EK = 16 / sizeof(K);
     const int tid = threadIdx.x;
@@ -203,19 +204,19 @@ __device__ __forceinline__ void store_tile(const TileView<K, VALS, NT, VT>& v, K
 #pragma unroll
                 for (int e = 0; e < EK; ++e) {
                     const int s = sidx[g * EK + e];
-                    w[e] = s < la ? sA[s] : sB[s - la];
+                    w[e] = key_out_ck<CK>(s < la ? sA[s] : sB[s - la], c);
                 }
                 st_global_cs_v4(gout + g * EK, *reinterpret_cast<uint4*>(w));
             }
         }
         for (int j = nvec * EK + tid; j < L; j += NT) {
             const int s = sidx[j];
-            gout[j] = s < la ? sA[s] : sB[s - la];
+            gout[j] = key_out_ck<CK>(s < la ? sA[s] : sB[s - la], c);
         }
     } else {
         for (int j = tid; j < L; j += NT) {
             const int s = sidx[j];
-            gout[j] = s < la ? sA[s] : sB[s - la];
+            gout[j] = key_out_ck<CK>(s < la ? sA[s] : sB[s - la], c);
         }
     }
     if constexpr (VALS) {

@@ -13,15 +13,29 @@
 #include "mp_device.cuh"
 #include "mp_internal.h"
 #include "mp_sort.cuh"
+#include "mp_bulk.cuh"
 
 namespace mp {
 
-template <class K, bool VALS, int NT, int VT>
+// ENC_OUT: the runs are written encoded (unsigned order), for the merge
+// passes that follow.
+template <class K, bool VALS, int NT, int VT, bool ENC_OUT>
 __global__ void __launch_bounds__(NT) block_sort_kernel(const K* in, const uint32_t* vin, K* out,
                                                         uint32_t* vout, int64_t n, Codec<K> c)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    block_sort_body<K, VALS, NT, VT>(in, vin, out, vout, n, c, blockIdx.x, smem);
+    block_sort_body<K, VALS, NT, VT, ENC_OUT>(in, vin, out, vout, n, c, blockIdx.x, smem);
+}
+
+// The last merge pass of a sort whose runs are encoded: keys are compared
+// as they are and decoded on output (an encoded-input codec kind CK); the
+// tile is merge_tile_bulk_body's, as in every other pass.
+template <class K, bool VALS, int NT, int VT, int CK>
+__global__ void __launch_bounds__(NT) sort_last_pass_kernel(TileArgs<K> p, unsigned int* err)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    merge_tile_bulk_body<K, VALS, NT, VT, CK>(p, blockIdx.x, p.a_split, smem, err);
 }
 
 // Per sort mode (key width, with or without values): the block-sort tile
@@ -84,12 +98,12 @@ size_t sort_workspace_bytes(const KeyKind& kind, int64_t n, bool with_values)
            align256((size_t)(tiles + 1) * 8);
 }
 
-template <class K, bool VALS, int NT, int VT>
+template <class K, bool VALS, int NT, int VT, bool ENC_OUT>
 static cudaError_t launch_block_sort(const K* in, const uint32_t* vin, K* out, uint32_t* vout,
                                      int64_t n, const KeyKind& kind, cudaStream_t stream)
 {
     using SM = SortSmem<K, VALS, NT, VT>;
-    auto kern = block_sort_kernel<K, VALS, NT, VT>;
+    auto kern = block_sort_kernel<K, VALS, NT, VT, ENC_OUT>;
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -106,24 +120,78 @@ static cudaError_t launch_block_sort(const K* in, const uint32_t* vin, K* out, u
 // Block-sort launch of one mode, its tile taken from the mode's macro.
 template <class K, bool VALS, int BNT, int BVT, int NT_, int VT_>
 static cudaError_t block_sort_mode(const void* in, const uint32_t* vin, void* out, uint32_t* vout,
-                                   int64_t n, const KeyKind& kind, cudaStream_t stream)
+                                   int64_t n, const KeyKind& kind, bool enc_out, cudaStream_t stream)
 {
-    return launch_block_sort<K, VALS, BNT, BVT>((const K*)in, vin, (K*)out, vout, n, kind, stream);
+    if (enc_out)
+        return launch_block_sort<K, VALS, BNT, BVT, true>((const K*)in, vin, (K*)out, vout, n, kind, stream);
+    return launch_block_sort<K, VALS, BNT, BVT, false>((const K*)in, vin, (K*)out, vout, n, kind, stream);
 }
 
 static cudaError_t block_sort(const KeyKind& kind, const void* in, const uint32_t* vin, void* out,
-                              uint32_t* vout, int64_t n, cudaStream_t stream)
+                              uint32_t* vout, int64_t n, bool enc_out, cudaStream_t stream)
 {
     if (kind.bytes == 4) {
-        if (vin) return block_sort_mode<uint32_t, true, MP_SORT_MODE_4V>(in, vin, out, vout, n, kind, stream);
-        return block_sort_mode<uint32_t, false, MP_SORT_MODE_4>(in, nullptr, out, nullptr, n, kind, stream);
+        if (vin) return block_sort_mode<uint32_t, true, MP_SORT_MODE_4V>(in, vin, out, vout, n, kind, enc_out, stream);
+        return block_sort_mode<uint32_t, false, MP_SORT_MODE_4>(in, nullptr, out, nullptr, n, kind, enc_out, stream);
     }
     if (kind.bytes == 16) {
-        if (vin) return block_sort_mode<u128, true, MP_SORT_MODE_16>(in, vin, out, vout, n, kind, stream);
-        return block_sort_mode<u128, false, MP_SORT_MODE_16>(in, nullptr, out, nullptr, n, kind, stream);
+        if (vin) return block_sort_mode<u128, true, MP_SORT_MODE_16>(in, vin, out, vout, n, kind, enc_out, stream);
+        return block_sort_mode<u128, false, MP_SORT_MODE_16>(in, nullptr, out, nullptr, n, kind, enc_out, stream);
     }
-    if (vin) return block_sort_mode<uint64_t, true, MP_SORT_MODE_8V>(in, vin, out, vout, n, kind, stream);
-    return block_sort_mode<uint64_t, false, MP_SORT_MODE_8>(in, nullptr, out, nullptr, n, kind, stream);
+    if (vin) return block_sort_mode<uint64_t, true, MP_SORT_MODE_8V>(in, vin, out, vout, n, kind, enc_out, stream);
+    return block_sort_mode<uint64_t, false, MP_SORT_MODE_8>(in, nullptr, out, nullptr, n, kind, enc_out, stream);
+}
+
+// Launch of the last pass over encoded runs (decoding codec fixed where the
+// kind allows).
+template <class K, bool VALS, int NT, int VT, int CK>
+static cudaError_t launch_last_pass_ck(const MergeProblem& p, const int64_t* a_split, cudaStream_t stream)
+{
+    using SM = MergeBulkSmem<K, VALS, NT, VT>;
+    auto kern = sort_last_pass_kernel<K, VALS, NT, VT, CK>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    unsigned int* err = kernel_error_word();
+    if (!err) return cudaErrorInvalidSymbol;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ceil_div(p.total(), (int64_t)NT * VT));
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = SM::bytes;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, make_tile_args<K>(p, a_split), err);
+}
+
+template <class K, bool VALS, int BNT, int BVT, int NT, int VT>
+static cudaError_t last_pass_mode(const MergeProblem& p, const int64_t* a_split, cudaStream_t stream)
+{
+    if (p.kind.signed_int()) return launch_last_pass_ck<K, VALS, NT, VT, CODEC_ENCODED_SIGNED>(p, a_split, stream);
+    if constexpr (sizeof(K) == 4) {
+        if (p.kind.ascending_float())
+            return launch_last_pass_ck<K, VALS, NT, VT, CODEC_ENCODED_FLOAT>(p, a_split, stream);
+    }
+    return launch_last_pass_ck<K, VALS, NT, VT, CODEC_ENCODED_RUNTIME>(p, a_split, stream);
+}
+
+static cudaError_t last_pass(const MergeProblem& p, const int64_t* a_split, cudaStream_t stream)
+{
+    const bool v = p.vals;
+    if (p.kind.bytes == 4)
+        return v ? last_pass_mode<uint32_t, true, MP_SORT_MODE_4V>(p, a_split, stream)
+                 : last_pass_mode<uint32_t, false, MP_SORT_MODE_4>(p, a_split, stream);
+    if (p.kind.bytes == 16)
+        return v ? last_pass_mode<u128, true, MP_SORT_MODE_16>(p, a_split, stream)
+                 : last_pass_mode<u128, false, MP_SORT_MODE_16>(p, a_split, stream);
+    return v ? last_pass_mode<uint64_t, true, MP_SORT_MODE_8V>(p, a_split, stream)
+             : last_pass_mode<uint64_t, false, MP_SORT_MODE_8>(p, a_split, stream);
 }
 
 mp_status sort_run(const KeyKind& kind, void* keys, uint32_t* vals, int64_t n, void* ws,
@@ -156,12 +224,19 @@ mp_status sort_run(const KeyKind& kind, void* keys, uint32_t* vals, int64_t n, v
     void* oth = (passes & 1) ? keys : ws_keys;
     uint32_t* othv = (passes & 1) ? vals : ws_vals;
 
-    cudaError_t e = block_sort(kind, keys, vals, cur, curv, n, stream);
+    // With merge passes to follow and a codec that is not the identity, the
+    // runs stay encoded between the passes: they compare as unsigned keys
+    // (no codec work in the intermediate passes) and the last pass decodes.
+    const bool encoded = passes > 0 && !kind.identity();
+    KeyKind plain = kind;
+    plain.flip = plain.fmask = plain.inv = 0;
+    cudaError_t e = block_sort(kind, keys, vals, cur, curv, n, encoded, stream);
     if (e != cudaSuccess) return cuda_fail(e, "block sort launch");
 
     for (int p = 0; p < passes; ++p) {
+        const bool last_decodes = encoded && p == passes - 1;
         MergeProblem mp;
-        mp.kind = kind;
+        mp.kind = encoded ? plain : kind;
         mp.vals = with_vals;
         mp.a = cur;
         mp.b = cur;
@@ -174,7 +249,12 @@ mp_status sort_run(const KeyKind& kind, void* keys, uint32_t* vals, int64_t n, v
         mp.run = bt << p;
         e = launch_partition(mp, ms.tile(), splits, stream);
         if (e != cudaSuccess) return cuda_fail(e, "sort pass partition launch");
-        e = launch_merge_tiles(mp, ms, splits, stream);
+        if (last_decodes) {
+            mp.kind = kind;  // compared as encoded, decoded with kind's codec
+            e = last_pass(mp, splits, stream);
+        } else {
+            e = launch_merge_tiles(mp, ms, splits, stream);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "sort pass merge launch");
         std::swap(cur, oth);
         std::swap(curv, othv);
