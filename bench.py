@@ -73,6 +73,8 @@ def parse_args():
     p.add_argument("--sort-log2-n", type=int, default=28, help="keys of the sort extra (log2)")
     p.add_argument("--tiles-log2-n", type=int, default=27, help="keys per side of the tiles extra (log2)")
     p.add_argument("--batched-segments", type=int, default=16384, help="segments of the batched extra")
+    p.add_argument("--setops-log2-universe", type=int, default=28,
+                   help="key universe of the set-operation extra (log2; each set holds about half)")
     return p.parse_args()
 
 
@@ -1047,7 +1049,7 @@ def run_ours(args):
                    "sort": lambda: extra_sort(mp, torch, dev, n=1 << args.sort_log2_n),
                    "batched": lambda: extra_batched(mp, torch, dev, n_seg=args.batched_segments),
                    "serving": lambda: extra_serving(mp, torch, dev, n_req=args.serving_requests),
-                   "setops": lambda: extra_setops(mp, torch, dev),
+                   "setops": lambda: extra_setops(mp, torch, dev, log2_universe=args.setops_log2_universe),
                    "wide": lambda: extra_wide(mp, torch, dev),
                    "crossover": lambda: extra_crossover(mp, torch, dev),
                    "tiles": lambda: extra_tiles(mp, torch, dev, log2_n=args.tiles_log2_n)}

@@ -292,14 +292,15 @@ MP_API int64_t mp_set_capacity(mp_setop op, int64_t na, int64_t nb);
  *   when values are given: any of a_vals, b_vals, out_vals non-NULL) hold
  *   mp_set_capacity(op, na, nb) elements, device, not overlapping an input.
  *   out_count: device pointer to one int64, set to the result length.
- * Kernels: the partition (Alg. 2 at every tile boundary, Cor. 6); a count
- * pass that merges each tile and counts the outputs it keeps; a scan of the
- * counts (in blocks of 1024 tiles); an emit pass that merges each tile
- * again and writes its kept outputs contiguously at the tile's offset (the
- * last tile also writes the result length).  Scratch from the library pool:
- * about 20 bytes per tile of 2048 outputs.  Asynchronous; inputs that are not sorted give an unspecified
- * subsequence and, where a tile's output would pass the capacity, set bit 2
- * of mp_kernel_error() (that tile writes nothing).
+ * Kernels: the partition (Alg. 2 at every tile boundary, Cor. 6), then one
+ * pass that merges each tile, decides which outputs it keeps, finds the
+ * tile's offset in the result from the kept counts of the tiles before it
+ * (a look-back over their published counts, tiles taken in order) and
+ * writes its kept outputs contiguously there (the last tile also writes the
+ * result length).  Scratch from the library pool: about 16 bytes per tile
+ * of 3968 to 15872 outputs.  Asynchronous; inputs that are not sorted give
+ * an unspecified subsequence and, where a tile's output would pass the
+ * capacity, set bit 2 of mp_kernel_error() (that tile writes nothing).
  */
 MP_API mp_status mp_set_operation(mp_setop op, mp_dtype dtype,
                                   const void* a_keys, const uint32_t* a_vals, int64_t na,
@@ -423,7 +424,9 @@ MP_API mp_status mp_graph_destroy(mp_graph* graph);
  * kernels whose bounded waits ran out (1: an mbarrier wait of a TMA-staged
  * merge timed out; the CTA stopped early and its tiles are incomplete;
  * 2: a set operation's tile output would pass the capacity, which only
- * unsorted inputs cause; that tile wrote nothing).
+ * unsorted inputs cause; that tile wrote nothing; 4: a set operation's
+ * bounded wait for an earlier tile's kept count ran out, which only follows
+ * flag 1; the tile's place in the output is wrong).
  * 0 means no kernel reported a problem since the last reset.  reset != 0
  * clears the flags after reading them.  (Robustness of this library; no
  * counterpart in the paper.)
@@ -432,8 +435,8 @@ MP_API mp_status mp_kernel_error(unsigned int* code, int reset);
 
 /*
  * mp_kernel_status -- waits for `stream`, then turns the flags of
- * mp_kernel_error into a status: MP_ERR_TIMEOUT if flag 1 is set (a staged
- * tile's bounded wait ran out, so some output was not written),
+ * mp_kernel_error into a status: MP_ERR_TIMEOUT if flag 1 or 4 is set (a
+ * bounded wait ran out, so some output was not written or misplaced),
  * MP_ERR_NOT_SORTED if flag 2 is set (a set operation met unsorted input),
  * else MP_OK.  reset != 0 clears the flags it read.  The flags are shared by
  * all streams of the device.  (Robustness of this library; no counterpart

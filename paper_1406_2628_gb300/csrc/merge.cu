@@ -393,6 +393,9 @@ extern "C" mp_status mp_kernel_status(mp_stream_t stream, int reset)
     if (v & MP_KERR_MBAR_TIMEOUT)
         return mp::fail(MP_ERR_TIMEOUT, "mp_kernel_status: a kernel's bounded wait for its staged "
                                         "tile ran out; that tile's output was not written");
+    if (v & 4u)
+        return mp::fail(MP_ERR_TIMEOUT, "mp_kernel_status: a set operation's bounded wait for an "
+                                        "earlier tile's count ran out; its output is misplaced");
     if (v & 2u)
         return mp::fail(MP_ERR_NOT_SORTED, "mp_kernel_status: a set operation's tile output "
                                            "passed the capacity (inputs not sorted)");

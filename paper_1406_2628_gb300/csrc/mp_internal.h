@@ -154,11 +154,11 @@ mp_status check_merge_args_ext(const KeyKind& k, const void* a, const uint32_t* 
                                const uint32_t* outv, bool vals, const char* fn, int64_t out_n = -1);
 
 // Merge-based set operations (setops.cu): splits from launch_partition with
-// spacing setop_tile(key bytes, values); counts (uint32) and offsets
-// (int64): one per tile.
+// spacing setop_tile(key bytes, values); status: one zeroed 64-bit word per
+// tile, tile_counter: one zeroed word.
 int64_t setop_tile(int key_bytes, bool vals);
-cudaError_t launch_setop(const MergeProblem& p, int op, const int64_t* splits, uint32_t* counts,
-                         int64_t* offsets, int64_t cap, int64_t* count, cudaStream_t stream);
+cudaError_t launch_setop(const MergeProblem& p, int op, const int64_t* splits, unsigned long long* status,
+                         unsigned int* tile_counter, int64_t cap, int64_t* count, cudaStream_t stream);
 
 // Read-only merge (results folded into a checksum, merge.cu).
 int64_t checksum_tile(int key_bytes, bool vals);
