@@ -190,6 +190,12 @@ MP_API int mp_plan_supported(const mp_plan* plan);
  * MP_STAGE_AUTO).  MP_ERR_INVALID_ARG for an unsupported plan or a NULL
  * resolved; MP_ERR_UNSUPPORTED_DTYPE for an unknown dtype.  (A library
  * query: the paper fixes the segment length as (|A|+|B|)/p, Alg. 1.)
+ * The environment variable MP_FORCE_PLAN="NT,VT[,staging]" (staging:
+ * vector, bulk, warp, stream or its MP_STAGE_* number), read at each call,
+ * replaces every automatic merge plan (for experiments; an unsupported one
+ * makes the calls return MP_ERR_INVALID_ARG).  Every public call and
+ * serving step is also an NVTX range named after the call, for profilers'
+ * timelines.
  */
 MP_API mp_status mp_merge_resolve_plan(mp_dtype dtype, int with_values, int64_t total, const mp_plan* plan,
                                        mp_plan* resolved);

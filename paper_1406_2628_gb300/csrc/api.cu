@@ -2,6 +2,7 @@
 // dispatch to the kernels, status strings and the sortedness check.
 #include <atomic>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -165,12 +166,37 @@ static bool plan_is_auto(const mp_plan* plan)
     return !plan || (!plan->block_threads && !plan->items_per_thread && !plan->staging && !plan->reserved);
 }
 
+// MP_FORCE_PLAN=NT,VT[,staging] (staging: vector, bulk, warp, stream or its
+// MP_STAGE_* number) replaces every automatic merge plan, for experiments;
+// read at each call.  Returns false when unset.
+static bool forced_plan(mp_plan* out)
+{
+    const char* env = getenv("MP_FORCE_PLAN");
+    if (!env || !*env) return false;
+    int nt = 0, vt = 0;
+    char stage[16] = {0};
+    const int got = sscanf(env, "%d,%d,%15s", &nt, &vt, stage);
+    if (got < 2) return false;
+    int st = 0;
+    if (got == 3) {
+        if (!strcmp(stage, "vector")) st = MP_STAGE_VECTOR;
+        else if (!strcmp(stage, "bulk")) st = MP_STAGE_BULK;
+        else if (!strcmp(stage, "warp")) st = MP_STAGE_WARP;
+        else if (!strcmp(stage, "stream")) st = MP_STAGE_STREAM;
+        else st = atoi(stage);
+    }
+    *out = mp_plan{nt, vt, st, 0};
+    return true;
+}
+
 // allow_stream: an automatic plan may pick the streaming merge (small
 // merges, where it saves the partition launch); callers that supply split
 // points pass false.
 static mp_status resolve_shape(const KeyKind& k, bool vals, int64_t total, const mp_plan* plan, Shape* s,
                                bool allow_stream = true)
 {
+    mp_plan forced;
+    if (plan_is_auto(plan) && forced_plan(&forced)) plan = &forced;
     if (plan_is_auto(plan)) {
         if (tuned_shape("merge", k.bytes, vals, total, s) && (allow_stream || s->staging != MP_STAGE_STREAM))
             return MP_OK;
@@ -196,7 +222,9 @@ static mp_status resolve_shape(const KeyKind& k, bool vals, int64_t total, const
     const bool ok = s->staging == MP_STAGE_STREAM ? stream_shape_supported(*s)
                                                   : merge_shape_supported(k.bytes, vals, *s);
     if (!ok)
-        return fail(MP_ERR_INVALID_ARG, "unsupported merge plan (block_threads, items_per_thread, staging)");
+        return fail(MP_ERR_INVALID_ARG, plan == &forced
+                                            ? "MP_FORCE_PLAN names an unsupported merge plan"
+                                            : "unsupported merge plan (block_threads, items_per_thread, staging)");
     return MP_OK;
 }
 
@@ -531,6 +559,7 @@ size_t mp_dtype_size(mp_dtype dtype)
 mp_status mp_merge_keys(mp_dtype dtype, const void* a, int64_t na, const void* b, int64_t nb,
                         void* out, mp_stream_t stream)
 {
+    MP_RANGE("mp_merge_keys");
     return merge_impl(dtype, a, nullptr, na, b, nullptr, nb, out, nullptr, false, nullptr,
                       (cudaStream_t)stream, "mp_merge_keys");
 }
@@ -539,6 +568,7 @@ mp_status mp_merge_pairs(mp_dtype dtype, const void* a_keys, const uint32_t* a_v
                          const void* b_keys, const uint32_t* b_vals, int64_t nb, void* out_keys,
                          uint32_t* out_vals, mp_stream_t stream)
 {
+    MP_RANGE("mp_merge_pairs");
     return merge_impl(dtype, a_keys, a_vals, na, b_keys, b_vals, nb, out_keys, out_vals, true, nullptr,
                       (cudaStream_t)stream, "mp_merge_pairs");
 }
@@ -547,6 +577,7 @@ mp_status mp_merge_plan(mp_dtype dtype, const void* a_keys, const uint32_t* a_va
                         const void* b_keys, const uint32_t* b_vals, int64_t nb, void* out_keys,
                         uint32_t* out_vals, const mp_plan* plan, mp_stream_t stream)
 {
+    MP_RANGE("mp_merge_plan");
     const bool vals = a_vals || b_vals || out_vals;
     return merge_impl(dtype, a_keys, a_vals, na, b_keys, b_vals, nb, out_keys, out_vals, vals, plan,
                       (cudaStream_t)stream, "mp_merge_plan");
@@ -588,6 +619,7 @@ mp_status mp_merge_partitioned(mp_dtype dtype, const void* a_keys, const uint32_
                                uint32_t* out_vals, const int64_t* a_split, const mp_plan* plan,
                                mp_stream_t stream)
 {
+    MP_RANGE("mp_merge_partitioned");
     if (na + nb > 0 && !a_split) return fail(MP_ERR_INVALID_ARG, "mp_merge_partitioned: NULL a_split");
     const bool vals = a_vals || b_vals || out_vals;
     return merge_impl(dtype, a_keys, a_vals, na, b_keys, b_vals, nb, out_keys, out_vals, vals, plan,
@@ -598,6 +630,7 @@ mp_status mp_merge_pairs_host(mp_dtype dtype, const void* a_keys, const uint32_t
                               const void* b_keys, const uint32_t* b_vals, int64_t nb, void* out_keys,
                               uint32_t* out_vals, mp_stream_t stream)
 {
+    MP_RANGE("mp_merge_pairs_host");
     KeyKind k;
     if (!key_kind(dtype, &k)) return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_merge_pairs_host: unknown dtype");
     const bool vals = a_vals || b_vals || out_vals;
@@ -613,6 +646,7 @@ mp_status mp_merge_checksum(mp_dtype dtype, const void* a_keys, const uint32_t* 
                             const void* b_keys, const uint32_t* b_vals, int64_t nb, uint64_t* checksum,
                             mp_stream_t stream)
 {
+    MP_RANGE("mp_merge_checksum");
     KeyKind k;
     if (!key_kind(dtype, &k) || k.bytes == 16)
         return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_merge_checksum: unknown or 128-bit dtype");
@@ -658,6 +692,7 @@ mp_status mp_merge_checksum(mp_dtype dtype, const void* a_keys, const uint32_t* 
 mp_status mp_merge_path_partition(mp_dtype dtype, const void* a, int64_t na, const void* b,
                                   int64_t nb, int64_t spacing, int64_t* a_split, mp_stream_t stream)
 {
+    MP_RANGE("mp_merge_path_partition");
     KeyKind k;
     if (!key_kind(dtype, &k)) return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_merge_path_partition: unknown dtype");
     if (na < 0 || nb < 0 || spacing < 1) return fail(MP_ERR_INVALID_ARG, "mp_merge_path_partition: bad size or spacing");
@@ -690,6 +725,7 @@ size_t mp_sort_workspace_bytes(mp_dtype dtype, int64_t n, int with_values)
 mp_status mp_sort(mp_dtype dtype, void* keys, uint32_t* vals, int64_t n, void* workspace,
                   size_t workspace_bytes, mp_stream_t stream)
 {
+    MP_RANGE("mp_sort");
     KeyKind k;
     if (!key_kind(dtype, &k)) return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_sort: unknown dtype");
     if (n < 0) return fail(MP_ERR_INVALID_ARG, "mp_sort: negative size");
@@ -708,6 +744,7 @@ mp_status mp_sort(mp_dtype dtype, void* keys, uint32_t* vals, int64_t n, void* w
 
 mp_status mp_check_sorted(mp_dtype dtype, const void* keys, int64_t n, mp_stream_t stream)
 {
+    MP_RANGE("mp_check_sorted");
     KeyKind k;
     if (!key_kind(dtype, &k)) return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_check_sorted: unknown dtype");
     if (n < 0 || (n > 0 && !keys)) return fail(MP_ERR_INVALID_ARG, "mp_check_sorted: bad arguments");

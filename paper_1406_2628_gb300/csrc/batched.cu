@@ -527,6 +527,7 @@ extern "C" mp_status mp_merge_batched(mp_dtype dtype, const void* a, const int64
                                       const uint32_t* a_vals, const uint32_t* b_vals,
                                       uint32_t* out_vals, const mp_plan* plan, mp_stream_t stream)
 {
+    MP_RANGE("mp_merge_batched");
     BatchedProblem q;
     Shape s;
     mp_status ms = batched_prepare(dtype, a, a_off, b, b_off, nseg, na_total, nb_total, out, a_vals,

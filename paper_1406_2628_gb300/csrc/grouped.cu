@@ -210,6 +210,7 @@ using namespace mp;
 extern "C" mp_status mp_merge_grouped(const mp_merge_desc* descs, int64_t nprob, int with_values,
                                       mp_stream_t stream)
 {
+    MP_RANGE("mp_merge_grouped");
     if (nprob < 0 || (nprob > 0 && !descs)) return fail(MP_ERR_INVALID_ARG, "mp_merge_grouped: bad descriptor array");
     if (nprob == 0) return MP_OK;
     if (nprob > (1 << 30)) return fail(MP_ERR_INVALID_ARG, "mp_merge_grouped: too many problems");

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "mp.h"
 
@@ -176,6 +177,16 @@ cudaError_t set_stage_wait_fault(bool on);
 // Host-side fault injection: true (and one fewer left) if the next event of
 // this mp_fault kind is to fail.
 bool take_fault(int kind);
+
+// An NVTX range around a public call or a serving step (shows up in a
+// profiler's timeline; without a profiler attached it costs a branch).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define MP_RANGE(name) ::mp::NvtxRange mp_nvtx_range_(name)
 
 // Errors: record a detail for mp_last_error() and return the status.
 mp_status fail(mp_status st, const std::string& detail);

@@ -65,6 +65,7 @@ extern "C" mp_status mp_merge_noalloc(mp_dtype dtype, const void* a_keys, const 
                                       int64_t nb, void* out_keys, uint32_t* out_vals,
                                       mp_stream_t stream)
 {
+    MP_RANGE("mp_merge_noalloc");
     // Written so that no sum can overflow: negative sizes are left to
     // merge_prepare's checks.
     if (na >= 0 && nb >= 0 && (na > kNoallocMaxTotal || nb > kNoallocMaxTotal - na))

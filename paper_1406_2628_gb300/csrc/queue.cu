@@ -289,6 +289,7 @@ static cudaError_t grow_tables(mp_queue* q, int slot, size_t bytes)
 // kernel launches.
 static cudaError_t run_step(mp_queue* q, std::vector<Job*>& work, int slot, uint64_t* launches)
 {
+    MP_RANGE("mp_queue step");
     // An injected fault (mp_inject_fault) fails the step the way a rejected
     // launch would, before anything is enqueued.
     if (take_fault(MP_FAULT_QUEUE_STEP)) return cudaErrorInvalidConfiguration;

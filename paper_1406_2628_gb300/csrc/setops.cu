@@ -893,6 +893,7 @@ mp_status mp_set_operation(mp_setop op, mp_dtype dtype, const void* a_keys, cons
                            const void* b_keys, const uint32_t* b_vals, int64_t nb, void* out_keys,
                            uint32_t* out_vals, int64_t* out_count, mp_stream_t stream)
 {
+    MP_RANGE("mp_set_operation");
     static const char* fn = "mp_set_operation";
     KeyKind k;
     if (!key_kind(dtype, &k)) return fail(MP_ERR_UNSUPPORTED_DTYPE, "mp_set_operation: unknown dtype");

@@ -189,3 +189,26 @@ def test_inject_fault_rejects_bad_arguments(lib):
     assert lib.mp_inject_fault(mp.MP_FAULT_SCRATCH_ALLOC, 3) == mp.MP_OK
     assert lib.mp_inject_fault(mp.MP_FAULT_SCRATCH_ALLOC, 0) == mp.MP_OK
     assert lib.mp_inject_fault(mp.MP_FAULT_QUEUE_STEP, 0) == mp.MP_OK
+
+
+def test_force_plan_override_of_automatic_plans(lib, monkeypatch):
+    # MP_FORCE_PLAN replaces the automatic plan (a host-side decision: no GPU).
+    big = 1 << 30
+    monkeypatch.delenv("MP_FORCE_PLAN", raising=False)
+    auto = mp.mp_merge_resolve_plan(mp.MP_U64, True, big)
+    assert auto[2] == mp.MP_STAGE_BULK
+    monkeypatch.setenv("MP_FORCE_PLAN", "128,8,vector")
+    assert mp.mp_merge_resolve_plan(mp.MP_U64, True, big) == (128, 8, mp.MP_STAGE_VECTOR)
+    monkeypatch.setenv("MP_FORCE_PLAN", "256,12,2")
+    assert mp.mp_merge_resolve_plan(mp.MP_I32, False, 1000) == (256, 12, mp.MP_STAGE_BULK)
+    # An explicit plan is not overridden.
+    assert mp.mp_merge_resolve_plan(mp.MP_U64, True, big, (128, 16, mp.MP_STAGE_BULK)) == \
+        (128, 16, mp.MP_STAGE_BULK)
+    # An unsupported forced plan is an argument error naming the variable.
+    monkeypatch.setenv("MP_FORCE_PLAN", "100,3,bulk")
+    with pytest.raises(mp.MPError) as ei:
+        mp.mp_merge_resolve_plan(mp.MP_U64, True, big)
+    assert ei.value.status == mp.MP_ERR_INVALID_ARG
+    assert "MP_FORCE_PLAN" in mp.mp_last_error()
+    monkeypatch.delenv("MP_FORCE_PLAN")
+    assert mp.mp_merge_resolve_plan(mp.MP_U64, True, big) == auto
