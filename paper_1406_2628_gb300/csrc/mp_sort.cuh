@@ -24,6 +24,7 @@
 #pragma once
 
 #include "mp_device.cuh"
+#include "mp_bulk.cuh"
 
 namespace mp {
 
@@ -53,7 +54,7 @@ struct SortSmem {
     static constexpr size_t keys_bytes = ((size_t)KEYS * sizeof(K) + 15) / 16 * 16;
     static constexpr size_t tags_bytes = ((size_t)TAGS * 2 + 15) / 16 * 16;
     static constexpr size_t vals_bytes = VALS ? (size_t)T * 4 : 0;
-    static constexpr size_t bytes = keys_bytes + tags_bytes + vals_bytes;
+    static constexpr size_t bytes = keys_bytes + tags_bytes + vals_bytes + 16;  // + mbarrier
 };
 
 // Compare-exchange of register slots a < b: order by key, then (with
@@ -158,11 +159,15 @@ __device__ __forceinline__ void bitonic_round_merge(const K* sk, int gs, int w, 
 
 // Sorts tile `tile` of in[0..n) into out (out may equal in: a CTA reads its
 // whole tile before writing).  ENC_OUT leaves the keys encoded (unsigned
-// order) for merge passes that compare them as they are.
-template <class K, bool VALS, int NT, int VT, bool ENC_OUT = false>
+// order) for merge passes that compare them as they are.  TMA_LOAD (keys
+// alone, unpadded layout): the tile arrives by one bulk copy on an mbarrier
+// (bounded wait; on a timeout flag 1 of *err is set and the tile is left
+// unwritten) instead of a loop of scalar loads, which with two CTAs per SM
+// kept too few bytes in flight to reach the HBM rate.
+template <class K, bool VALS, int NT, int VT, bool ENC_OUT = false, bool TMA_LOAD = false>
 __device__ __forceinline__ void block_sort_body(const K* in, const uint32_t* vin, K* out,
                                                 uint32_t* vout, int64_t n, Codec<K> c, int64_t tile,
-                                                unsigned char* smem)
+                                                unsigned char* smem, unsigned int* err = nullptr)
 {
     static_assert((NT & (NT - 1)) == 0, "NT must be a power of two");
     using SM = SortSmem<K, VALS, NT, VT>;
@@ -177,24 +182,61 @@ __device__ __forceinline__ void block_sort_body(const K* in, const uint32_t* vin
     const int L = (int)(n - base < T ? n - base : T);
     const K pad = ~K(0);  // encoded maximum: sorts after every real key
 
-    // 1. Coalesced load; positions past the end hold the padding key.
-#pragma unroll 4
-    for (int j = tid; j < T; j += NT) {
-        sk[padded<K, PAD>(j)] = j < L ? key_enc(in[base + j], c) : pad;
-        if constexpr (VALS) {
-            if (j < L) sv[j] = vin[base + j];
-        }
-    }
-    __syncthreads();
-
-    // 2. Thread-local sort of VT keys.
     K keys[VT];
     uint16_t tags[VT];
+    bool loaded = false;
+    if constexpr (TMA_LOAD && !VALS && !PAD) {
+        const K* src = in + base;
+        if (((uintptr_t)src & 15) == 0) {  // the same for every thread of the CTA
+            // 1. The tile's 16-byte-aligned body by one bulk copy, its
+            //    ragged end (< 16 bytes) by threads; read back and encoded
+            //    per thread, positions past the end taking the padding key.
+            constexpr int EK = 16 / sizeof(K);
+            constexpr uint32_t WAIT_LIMIT = 1u << 22;
+            uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::bytes - 16);
+            const int nmain = (L / EK) * EK;
+            bulk_init(bar);
+            __syncthreads();
+            if (tid == 0) {
+                mbar_arrive_expect_tx(bar, (uint32_t)(nmain * sizeof(K)));
+                if (nmain) bulk_g2s(sk, src, (uint32_t)(nmain * sizeof(K)), bar);
+            }
+            if (tid < L - nmain) sk[nmain + tid] = src[nmain + tid];
+            // err[1] is the staging-wait fault switch (see bulk_stage).
+            const uint32_t first_limit = __ldcg(err + 1) ? 0u : WAIT_LIMIT;
+            const bool ok = __syncthreads_and(mbar_wait_bounded(bar, 0, first_limit));
+            if (!ok) {
+                if (tid == 0) atomicOr(err, MP_KERR_MBAR_TIMEOUT);
+                mbar_wait_bounded(bar, 0, WAIT_LIMIT);  // let copies in flight land
+                return;
+            }
 #pragma unroll
-    for (int i = 0; i < VT; ++i) {
-        keys[i] = sk[padded<K, PAD>(tid * VT + i)];
-        tags[i] = (uint16_t)(tid * VT + i);
+            for (int i = 0; i < VT; ++i) {
+                const int j = tid * VT + i;
+                keys[i] = j < L ? key_enc(sk[j], c) : pad;
+                tags[i] = (uint16_t)j;
+            }
+            loaded = true;
+        }
     }
+    if (!loaded) {
+        // 1. Coalesced load; positions past the end hold the padding key.
+#pragma unroll 4
+        for (int j = tid; j < T; j += NT) {
+            sk[padded<K, PAD>(j)] = j < L ? key_enc(in[base + j], c) : pad;
+            if constexpr (VALS) {
+                if (j < L) sv[j] = vin[base + j];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < VT; ++i) {
+            keys[i] = sk[padded<K, PAD>(tid * VT + i)];
+            tags[i] = (uint16_t)(tid * VT + i);
+        }
+    }
+
+    // 2. Thread-local sort of VT keys.
     register_sort<K, VALS, VT>(keys, tags);
 
     // 3. Merge rounds: runs of width w = VT * 2^r merge pairwise; the pair

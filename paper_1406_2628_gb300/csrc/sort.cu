@@ -21,10 +21,11 @@ namespace mp {
 // passes that follow.
 template <class K, bool VALS, int NT, int VT, bool ENC_OUT>
 __global__ void __launch_bounds__(NT) block_sort_kernel(const K* in, const uint32_t* vin, K* out,
-                                                        uint32_t* vout, int64_t n, Codec<K> c)
+                                                        uint32_t* vout, int64_t n, Codec<K> c,
+                                                        unsigned int* err)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    block_sort_body<K, VALS, NT, VT, ENC_OUT>(in, vin, out, vout, n, c, blockIdx.x, smem);
+    block_sort_body<K, VALS, NT, VT, ENC_OUT, true>(in, vin, out, vout, n, c, blockIdx.x, smem, err);
 }
 
 // The last merge pass of a sort whose runs are encoded: keys are compared
@@ -111,9 +112,11 @@ static cudaError_t launch_block_sort(const K* in, const uint32_t* vin, K* out, u
         if (e != cudaSuccess) return e;
         configured = true;
     }
+    unsigned int* err = kernel_error_word();
+    if (!err) return cudaErrorInvalidSymbol;
     const Codec<K> c = make_codec<K>(kind.flip, kind.fmask, kind.inv);
     const int64_t blocks = ceil_div(n, (int64_t)NT * VT);
-    kern<<<(unsigned)blocks, NT, SM::bytes, stream>>>(in, vin, out, vout, n, c);
+    kern<<<(unsigned)blocks, NT, SM::bytes, stream>>>(in, vin, out, vout, n, c, err);
     return cudaGetLastError();
 }
 
