@@ -103,8 +103,7 @@ __device__ __forceinline__ BatchTile batch_tile(const BatchArgs<K>& p, int64_t t
     t.d0 = tile * T;
     const int64_t d1 = t.d0 + T < p.total ? t.d0 + T : p.total;
     t.a0 = clamp_split(p.a_split[tile], t.d0, p.na, p.nb);
-    int64_t a1 = clamp_split(p.a_split[tile + 1], d1, p.na, p.nb);
-    t.a1 = a1 < t.a0 ? t.a0 : (a1 > t.a0 + (d1 - t.d0) ? t.a0 + (d1 - t.d0) : a1);
+    t.a1 = clamp_end_split(p.a_split[tile + 1], t.a0, t.d0, d1, p.na, p.nb);
     t.b0 = t.d0 - t.a0;
     t.b1 = d1 - t.a1;
     int64_t s0 = p.seg_split[tile], s1 = p.seg_split[tile + 1];

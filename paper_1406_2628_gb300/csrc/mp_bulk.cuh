@@ -82,8 +82,7 @@ __device__ __forceinline__ TilePlace<K> tile_place(const TileArgs<K>& p, int64_t
     const Pair<K> q = pair_at(p, d0);
     const int64_t d0l = d0 - q.base, d1l = d1 - q.base;
     const int64_t a0 = clamp_split(a_split[tile], d0l, q.na, q.nb);
-    int64_t a1 = (d1l == q.na + q.nb) ? q.na : clamp_split(a_split[tile + 1], d1l, q.na, q.nb);
-    a1 = a1 < a0 ? a0 : (a1 > a0 + (d1l - d0l) ? a0 + (d1l - d0l) : a1);
+    const int64_t a1 = (d1l == q.na + q.nb) ? q.na : clamp_end_split(a_split[tile + 1], a0, d0l, d1l, q.na, q.nb);
     const int64_t b0 = d0l - a0, b1 = d1l - a1;
     TilePlace<K> t;
     t.gA = q.A + a0;
@@ -169,19 +168,20 @@ __device__ __forceinline__ EdgeLoad<E> edge_load(int j, const E* gA, int la, con
 }
 
 // Shared memory of a TMA-staged tile: keys, values (if VALS), the T source
-// indices (if IDX) and the mbarrier.
-template <class K, bool VALS, int NT, int VT, bool IDX = true>
+// indices (if IDX) and the mbarrier.  SLACK: extra key slots after the
+// windows, for walks that may read up to that far past them.
+template <class K, bool VALS, int NT, int VT, bool IDX = true, int SLACK = 0>
 struct BulkSmem {
     static constexpr int T = NT * VT;
     static constexpr int EK = 16 / sizeof(K);
-    static constexpr size_t keys_bytes = ((size_t)(T + 3 * EK) * sizeof(K) + 15) / 16 * 16;
+    static constexpr size_t keys_bytes = ((size_t)(T + 3 * EK + SLACK) * sizeof(K) + 15) / 16 * 16;
     static constexpr size_t vals_bytes = VALS ? ((size_t)(T + 12) * 4 + 15) / 16 * 16 : 0;
     static constexpr size_t idx_bytes = IDX ? ((size_t)T * 2 + 15) / 16 * 16 : 0;
     static constexpr size_t bytes = keys_bytes + vals_bytes + idx_bytes + 16;  // + mbarrier
 };
 
 // Shared-memory regions of a TMA-staged tile (sidx is null without IDX).
-template <class K, bool VALS, int NT, int VT, bool IDX = true>
+template <class K, bool VALS, int NT, int VT, bool IDX = true, int SLACK = 0>
 struct BulkLayout {
     K* sk;
     uint32_t* sv;
@@ -189,7 +189,7 @@ struct BulkLayout {
     uint64_t* bar;
     __device__ __forceinline__ explicit BulkLayout(unsigned char* smem)
     {
-        using SM = BulkSmem<K, VALS, NT, VT, IDX>;
+        using SM = BulkSmem<K, VALS, NT, VT, IDX, SLACK>;
         sk = reinterpret_cast<K*>(smem);
         sv = reinterpret_cast<uint32_t*>(smem + SM::keys_bytes);
         sidx = IDX ? reinterpret_cast<uint16_t*>(smem + SM::keys_bytes + SM::vals_bytes) : nullptr;

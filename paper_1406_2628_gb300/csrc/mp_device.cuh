@@ -308,6 +308,22 @@ __device__ __forceinline__ int64_t clamp_split(int64_t a, int64_t d, int64_t na,
     return a < lo ? lo : (a > hi ? hi : a);
 }
 
+// A tile's end split from its start split a0 (on diagonal d0, already in
+// the grid) and a raw end split a1 on d1: in the grid on d1 and in
+// [a0, a0 + (d1 - d0)], so that both windows, A[a0, a1) and
+// B[d0 - a0, d1 - a1), stay inside their arrays whatever the split array
+// holds (splits of unsorted input, or a caller's foreign ones, need not be
+// monotone).  For valid splits nothing changes.
+__device__ __forceinline__ int64_t clamp_end_split(int64_t a1, int64_t a0, int64_t d0, int64_t d1, int64_t na,
+                                                   int64_t nb)
+{
+    a1 = clamp_split(a1, d1, na, nb);
+    a1 = a1 < a0 ? a0 : a1;
+    a1 = a1 > a0 + (d1 - d0) ? a0 + (d1 - d0) : a1;
+    const int64_t lo1 = d1 - nb > 0 ? d1 - nb : 0;  // at most a0 + (d1 - d0), as a0 >= d0 - nb
+    return a1 < lo1 ? lo1 : a1;
+}
+
 // 32-bit version for searches inside shared memory.
 template <class K>
 __device__ __forceinline__ int smem_diagonal_search(const K* sA, int la, const K* sB, int lb,

@@ -291,8 +291,7 @@ __device__ __forceinline__ void merge_tile_body(const TileArgs<K>& p, int64_t ti
     // unsorted inputs or foreign split arrays give wrong output rather than
     // out-of-range accesses; for valid inputs the clamps change nothing.
     const int64_t a0 = clamp_split(a_split[tile], d0l, q.na, q.nb);
-    int64_t a1 = (d1l == q.na + q.nb) ? q.na : clamp_split(a_split[tile + 1], d1l, q.na, q.nb);
-    a1 = a1 < a0 ? a0 : (a1 > a0 + (d1l - d0l) ? a0 + (d1l - d0l) : a1);
+    const int64_t a1 = (d1l == q.na + q.nb) ? q.na : clamp_end_split(a_split[tile + 1], a0, d0l, d1l, q.na, q.nb);
     const int64_t b0 = d0l - a0, b1 = d1l - a1;
     const int la = (int)(a1 - a0), lb = (int)(b1 - b0);
     const int L = la + lb;

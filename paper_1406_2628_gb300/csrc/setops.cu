@@ -108,7 +108,12 @@ struct SetCtx {
 
 template <class K, bool VALS, int NT, int VT>
 struct SetSmem {
-    using B = BulkSmem<K, VALS, NT, VT, VALS>;  // source indices only with values
+    // Source indices only with values.  Without values, VT + 1 spare key
+    // slots: the walk without end tests (setop_walk_keys) reads at most VT + 1
+    // past its start, which for unsorted inputs (a broken precondition) can lie
+    // past the windows; the slots keep those reads inside the array.
+    static constexpr int SLACK = VALS ? 0 : VT + 1;
+    using B = BulkSmem<K, VALS, NT, VT, VALS, SLACK>;
     static constexpr size_t ctx_off = (B::bytes + 15) / 16 * 16;
     static constexpr size_t scan_off = ctx_off + (sizeof(SetCtx<K>) + 15) / 16 * 16;
     static constexpr size_t split_off = scan_off + (NT / 32 + 4) * 8;  // NT thread splits
@@ -440,7 +445,7 @@ __device__ __forceinline__ bool setop_tile_prepare(const SetArgs<K>& p, int64_t 
     using SM = SetSmem<K, VALS, NT, VT>;
     constexpr int T = NT * VT;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const BulkLayout<K, VALS, NT, VT, VALS> lay(smem);
+    const BulkLayout<K, VALS, NT, VT, VALS, SetSmem<K, VALS, NT, VT>::SLACK> lay(smem);
     SetCtx<K>& x = *reinterpret_cast<SetCtx<K>*>(smem + SM::ctx_off);
     const TileArgs<K>& ta = p.t;
     t = tile_place(ta, tile, T, ta.a_split);
@@ -510,7 +515,7 @@ __device__ __forceinline__ bool setop_tile_walk(const SetArgs<K>& p, int64_t til
     using SM = SetSmem<K, VALS, NT, VT>;
     constexpr int T = NT * VT;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const BulkLayout<K, VALS, NT, VT, VALS> lay(smem);
+    const BulkLayout<K, VALS, NT, VT, VALS, SetSmem<K, VALS, NT, VT>::SLACK> lay(smem);
     SetCtx<K>& x = *reinterpret_cast<SetCtx<K>*>(smem + SM::ctx_off);
     const TileArgs<K>& ta = p.t;
     t = tile_place(ta, tile, T, ta.a_split);
@@ -735,7 +740,7 @@ __global__ void __launch_bounds__(NT, (sizeof(K) == 4 ? 1024 : 512) / NT)
         constexpr int EK = 16 / sizeof(K);
         K* gout = ta.out + g;
         int pos = (int)scan[warp] + incl - c;
-        const BulkLayout<K, VALS, NT, VT, VALS> lay(smem);
+        const BulkLayout<K, VALS, NT, VT, VALS, SetSmem<K, VALS, NT, VT>::SLACK> lay(smem);
         K* so = lay.sk;
         const int ph = phase16(gout);
 #pragma unroll

@@ -283,8 +283,11 @@ __global__ void __launch_bounds__(NT) merge_stream_kernel(StreamArgs<K> p, unsig
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    // The end split kept consistent with the start (see clamp_end_split), so
+    // that the share's windows lie inside A and B even for unsorted input.
     const int64_t a0 = ctl[0], b0 = d_start - a0;
-    const uint32_t nA = (uint32_t)(ctl[1] - a0), nB = (uint32_t)((d_end - ctl[1]) - b0);
+    const int64_t a_end = clamp_end_split(ctl[1], a0, d_start, d_end, p.na, p.nb);
+    const uint32_t nA = (uint32_t)(a_end - a0), nB = (uint32_t)((d_end - a_end) - b0);
     const Ring<K> rkA{skA, p.a + a0, (uint32_t)phase16(p.a + a0)};
     const Ring<K> rkB{skB, p.b + b0, (uint32_t)phase16(p.b + b0)};
     Ring<uint32_t> rvA{svA, nullptr, 0}, rvB{svB, nullptr, 0};
@@ -366,7 +369,12 @@ __global__ void __launch_bounds__(NT) merge_stream_kernel(StreamArgs<K> p, unsig
         const int64_t d = d_start + (int64_t)k * T;
         ring_store<K, VALS, NT, VT, C>(skA, kbA, skB, kbB, svA, vbA, svB, vbB, la, Lk, sidx, p.out + d,
                                        VALS ? p.outv + d : nullptr);
-        const uint32_t adv = (uint32_t)ctl[2];
+        // A taken by this step; for sorted input exactly the path's, and
+        // otherwise kept inside what remains of the share on each side (the
+        // remainder holds at least T before the last step).
+        uint32_t adv = (uint32_t)ctl[2];
+        if ((uint32_t)T - adv > nB - b) adv = (uint32_t)T - (nB - b);
+        if (adv > nA - a) adv = nA - a;
         a += adv;
         b += (uint32_t)T - adv;
         __syncthreads();  // rings and indices are free for the next batch and step
