@@ -303,8 +303,10 @@ MP_API int64_t mp_set_capacity(mp_setop op, int64_t na, int64_t nb);
  * tile's offset in the result from the kept counts of the tiles before it
  * (a look-back over their published counts, tiles taken in order) and
  * writes its kept outputs contiguously there (the last tile also writes the
- * result length).  Scratch from the library pool: about 16 bytes per tile
- * of 3968 to 15872 outputs.  Asynchronous; inputs that are not sorted give
+ * result length); without values the pass runs on one or two persistent
+ * CTAs per SM that overlap the copies, walks, look-backs and stores of
+ * consecutive tiles.  Scratch from the library pool: about 16 bytes per tile
+ * of 2048 to 8832 outputs.  Asynchronous; inputs that are not sorted give
  * an unspecified subsequence and, where a tile's output would pass the
  * capacity, set bit 2 of mp_kernel_error() (that tile writes nothing).
  */

@@ -11,21 +11,25 @@
 // of equal keys on its own side and on the length of that key's run on the
 // other side, so the method is the merge with a decision per output:
 //   1. partition: Alg. 2 at every tile boundary (Cor. 6, as for the merge);
-//   2. per tile (one CTA): stage the windows A[a0,a1), B[b0,b1) in shared
-//      memory (TMA bulk copies, Lemma 16); each thread finds its split in
-//      the windows (Thm 17), walks its VT outputs of S and decides each one.
+//   2. per tile: stage the windows A[a0,a1), B[b0,b1) in shared memory
+//      (TMA bulk copies, Lemma 16); each thread finds its split in the
+//      windows (Thm 17), walks its VT outputs of S and decides each one.
 //      Runs are measured inside the windows; a run that crosses a window
 //      edge is completed with three galloping searches in global memory per
 //      tile (the run ending at a0-1 in A, at b0-1 in B, the run starting at
-//      b1 in B), done while the copies are in flight;
+//      b1 in B);
 //   3. placement: tiles are taken in order from a counter; each publishes
 //      its kept count as soon as its walk is done and adds up the counts of
 //      the tiles before it back to the nearest one that has published its
-//      inclusive prefix (a decoupled look-back); its kept outputs are then
+//      inclusive prefix (a decoupled look-back); its kept outputs are
 //      compacted in shared memory and written at that offset.  One pass over
 //      the inputs.  (A count pass + scan + emit pass, which reads the inputs
 //      twice and walks every tile twice, measured slower: 0.89 ms against
 //      0.82 ms for the union of two 2^27-key sets.)
+// Tiles of keys alone run in a persistent kernel whose CTAs overlap the
+// copies, walk, look-back and store of consecutive tiles (setop_keys_kernel:
+// 0.81 -> 0.68 ms for that union); tiles with values run one per CTA
+// (setop_kernel).
 #include <algorithm>
 
 #include "mp_bulk.cuh"
@@ -106,14 +110,11 @@ struct SetCtx {
     int has_prev_a, has_prev_b, has_next_a, has_next_b;
 };
 
+// Shared memory of a tile with values (setop_kernel): the staged windows with
+// their source indices, the run context, the scan and the thread splits.
 template <class K, bool VALS, int NT, int VT>
 struct SetSmem {
-    // Source indices only with values.  Without values, VT + 1 spare key
-    // slots: the walk without end tests (setop_walk_keys) reads at most VT + 1
-    // past its start, which for unsorted inputs (a broken precondition) can lie
-    // past the windows; the slots keep those reads inside the array.
-    static constexpr int SLACK = VALS ? 0 : VT + 1;
-    using B = BulkSmem<K, VALS, NT, VT, VALS, SLACK>;
+    using B = BulkSmem<K, VALS, NT, VT, true>;
     static constexpr size_t ctx_off = (B::bytes + 15) / 16 * 16;
     static constexpr size_t scan_off = ctx_off + (sizeof(SetCtx<K>) + 15) / 16 * 16;
     static constexpr size_t split_off = scan_off + (NT / 32 + 4) * 8;  // NT thread splits
@@ -434,78 +435,8 @@ __device__ __forceinline__ uint32_t setop_walk_keys(const K* sA, int la, const K
     return keep & valid;
 }
 
-// Stage tile `tile` and find the runs crossing the window edges; sets this
-// thread's split (ai, its diagonal diag) in the windows.  Returns false (all
-// threads) if the staging wait ran out.
-template <class K, bool VALS, int NT, int VT, int CK>
-__device__ __forceinline__ bool setop_tile_prepare(const SetArgs<K>& p, int64_t tile, unsigned char* smem,
-                                                   unsigned int* err, TilePlace<K>& t,
-                                                   TileView<K, VALS, NT, VT>& v, int& ai, int& diag)
-{
-    using SM = SetSmem<K, VALS, NT, VT>;
-    constexpr int T = NT * VT;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const BulkLayout<K, VALS, NT, VT, VALS, SetSmem<K, VALS, NT, VT>::SLACK> lay(smem);
-    SetCtx<K>& x = *reinterpret_cast<SetCtx<K>*>(smem + SM::ctx_off);
-    const TileArgs<K>& ta = p.t;
-    t = tile_place(ta, tile, T, ta.a_split);
-    v = stage_view<K, VALS, NT, VT>(t, lay.sk, lay.sv, lay.sidx);
-    const int64_t a0 = t.gA - ta.a, b0 = t.gB - ta.b;
-    const int64_t b1 = b0 + t.lb;
-    bulk_init(lay.bar);
-    __syncthreads();
-    if (warp == 3) {  // the keys just outside the windows, while the copies fly
-        if (lane == 0) {
-            x.has_prev_a = a0 > 0;
-            if (a0 > 0) x.prev_a = ld_global_nc(ta.a + a0 - 1);
-        } else if (lane == 1) {
-            x.has_prev_b = b0 > 0;
-            if (b0 > 0) x.prev_b = ld_global_nc(ta.b + b0 - 1);
-        } else if (lane == 2) {
-            x.has_next_b = b1 < ta.nb;
-            if (b1 < ta.nb) x.next_b = ld_global_nc(ta.b + b1);
-        } else if (lane == 3) {
-            const int64_t a1 = a0 + t.la;
-            x.has_next_a = a1 < ta.na;
-            if (a1 < ta.na) x.next_a = ld_global_nc(ta.a + a1);
-        }
-    }
-    // The staging barrier also publishes x.
-    if (!bulk_stage<K, VALS, NT, VT>(t, v, lay.bar, 0, err)) return false;
-    // Run lengths are consulted only for outputs whose key repeats on its own
-    // side and occurs on the other (setop_slow).  A run crossing a window
-    // edge is then measured in global memory, once per tile (the condition
-    // is the same on every thread): the run ending at a0-1 in A when A's
-    // window starts inside it, or when B's window starts with its key and
-    // that key repeats in B; the run ending at b0-1 in B when B's window
-    // starts inside it; the run starting at b1 in B when B's window ends
-    // inside it, or when A's window ends with its key and that key repeats
-    // in A.  Duplicate-free inputs never need them.
-    const int la = t.la, lb = t.lb;
-    const bool b0_rep = lb > 0 && ((lb > 1 && v.sB[1] == v.sB[0]) || (x.has_prev_b && x.prev_b == v.sB[0]));
-    const bool a_end_rep =
-        la > 0 && ((la > 1 && v.sA[la - 2] == v.sA[la - 1]) || (la == 1 && x.has_prev_a && x.prev_a == v.sA[0]));
-    const bool need_a = x.has_prev_a && ((la > 0 && v.sA[0] == x.prev_a) || (b0_rep && v.sB[0] == x.prev_a));
-    const bool need_b = x.has_prev_b && lb > 0 && v.sB[0] == x.prev_b;
-    const bool need_n = x.has_next_b &&
-                        ((lb > 0 && v.sB[lb - 1] == x.next_b) || (a_end_rep && v.sA[la - 1] == x.next_b));
-    if (need_a || need_b || need_n) {
-        if (warp == 3) {
-            if (lane == 0 && need_a) x.lb_prev_a = run_start(ta.a, a0 - 1);
-            if (lane == 1 && need_b) x.lb_prev_b = run_start(ta.b, b0 - 1);
-            if (lane == 2 && need_n) x.ub_next_b = run_end(ta.b, ta.nb, b1);
-        }
-        __syncthreads();
-    }
-    const int L = t.la + t.lb;
-    diag = tid * VT < L ? tid * VT : L;
-    ai = smem_diagonal_search_ck<CK>(v.sA, t.la, v.sB, t.lb, diag, ta.codec);
-    return true;
-}
-
-// Stage, split and walk with source indices (tiles with values): the same
-// staging as setop_tile_prepare, kept in one piece.  Returns false (all threads) if the staging wait ran
-// out.
+// Stage, split and walk with source indices (tiles with values).  Returns
+// false (all threads) if the staging wait ran out.
 template <class K, bool VALS, int NT, int VT, int CK>
 __device__ __forceinline__ bool setop_tile_walk(const SetArgs<K>& p, int64_t tile, unsigned char* smem,
                                                 unsigned int* err, TilePlace<K>& t,
@@ -515,7 +446,7 @@ __device__ __forceinline__ bool setop_tile_walk(const SetArgs<K>& p, int64_t til
     using SM = SetSmem<K, VALS, NT, VT>;
     constexpr int T = NT * VT;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const BulkLayout<K, VALS, NT, VT, VALS, SetSmem<K, VALS, NT, VT>::SLACK> lay(smem);
+    const BulkLayout<K, VALS, NT, VT, true> lay(smem);
     SetCtx<K>& x = *reinterpret_cast<SetCtx<K>*>(smem + SM::ctx_off);
     const TileArgs<K>& ta = p.t;
     t = tile_place(ta, tile, T, ta.a_split);
@@ -572,33 +503,6 @@ __device__ __forceinline__ bool setop_tile_walk(const SetArgs<K>& p, int64_t til
     const int ai = smem_diagonal_search_ck<CK>(v.sA, t.la, v.sB, t.lb, diag, ta.codec);
     keep = setop_walk<K, VT, CK>(v.sA, t.la, v.sB, t.lb, ai, diag - ai, L - diag, p.op, x, a0, b0,
                                       ta.codec, packed);
-    return true;
-}
-
-// Stage, split and walk with the merged keys kept in registers (tiles
-// without values; the count pass of every tile).
-template <class K, bool VALS, int NT, int VT, int CK, bool KEEP>
-__device__ __forceinline__ bool setop_tile_walk_keys(const SetArgs<K>& p, int64_t tile, unsigned char* smem,
-                                                     unsigned int* err, TilePlace<K>& t,
-                                                     TileView<K, VALS, NT, VT>& v, K (&keys)[KEEP ? VT : 1],
-                                                     uint32_t& keep)
-{
-    using SM = SetSmem<K, VALS, NT, VT>;
-    int ai, diag;
-    if (!setop_tile_prepare<K, VALS, NT, VT, CK>(p, tile, smem, err, t, v, ai, diag)) return false;
-    const SetCtx<K>& x = *reinterpret_cast<const SetCtx<K>*>(smem + SM::ctx_off);
-    const int64_t a0 = t.gA - p.t.a, b0 = t.gB - p.t.b;
-    const int L = t.la + t.lb;
-    // The share's end split is the next thread's start split.
-    int* split = reinterpret_cast<int*>(smem + SM::split_off);
-    const int tid = threadIdx.x;
-    split[tid] = ai;
-    __syncthreads();
-    const int dend = diag + VT;
-    const int ai_end = tid + 1 < NT ? split[tid + 1] : t.la;
-    const bool inside = dend < L && ai_end < t.la && dend - ai_end < t.lb;
-    keep = setop_walk_keys<K, VT, CK, KEEP>(v.sA, t.la, v.sB, t.lb, ai, diag - ai, L - diag, inside, p.op, x,
-                                            a0, b0, p.t.codec, keys);
     return true;
 }
 
@@ -664,9 +568,10 @@ __device__ __forceinline__ unsigned long long lookback(unsigned long long* statu
     return prefix;
 }
 
-// The set-operation tile kernel: take the next tile in order, stage it,
-// walk and decide its outputs, publish its kept count and look back for its
-// place, write the kept outputs there.
+// The set-operation tile kernel for tiles with values (one tile per CTA):
+// take the next tile in order, stage it, walk and decide its outputs,
+// publish its kept count and look back for its place, write the kept
+// outputs and their values there.
 template <class K, bool VALS, int NT, int VT, int CK>
 __global__ void __launch_bounds__(NT, (sizeof(K) == 4 ? 1024 : 512) / NT)
     setop_kernel(SetArgs<K> p, unsigned int* err)
@@ -683,14 +588,9 @@ __global__ void __launch_bounds__(NT, (sizeof(K) == 4 ? 1024 : 512) / NT)
     TilePlace<K> t;
     TileView<K, VALS, NT, VT> v;
     uint32_t keep = 0;
-    uint32_t packed[(VT + 1) / 2];  // with values: the outputs' sources
-    K keys[VALS ? 1 : VT];          // without values: the merged keys
-    bool ok;
-    if constexpr (VALS)
-        ok = setop_tile_walk<K, VALS, NT, VT, CK>(p, tile, smem, err, t, v, packed, keep);
-    else
-        ok = setop_tile_walk_keys<K, VALS, NT, VT, CK, true>(p, tile, smem, err, t, v, keys, keep);
-    if (!ok) {
+    static_assert(VALS, "tiles of keys alone run in setop_keys_kernel");
+    uint32_t packed[(VT + 1) / 2];  // the outputs' sources
+    if (!setop_tile_walk<K, VALS, NT, VT, CK>(p, tile, smem, err, t, v, packed, keep)) {
         // The tile stopped on a failed staging wait: publish it as empty so
         // that later tiles do not wait for it.
         if (tid == 0) st_relaxed_u64(p.status + tile, (tile == 0 ? LB_INC : LB_AGG));
@@ -733,53 +633,407 @@ __global__ void __launch_bounds__(NT, (sizeof(K) == 4 ? 1024 : 512) / NT)
         return;
     }
     const TileArgs<K>& ta = p.t;
-    if constexpr (!VALS) {
-        // The kept keys replace the windows in shared memory, at the 16-byte
-        // phase of their destination, and leave with 128-bit stores (the
-        // partial vectors at both ends element by element).
-        constexpr int EK = 16 / sizeof(K);
-        K* gout = ta.out + g;
-        int pos = (int)scan[warp] + incl - c;
-        const BulkLayout<K, VALS, NT, VT, VALS, SetSmem<K, VALS, NT, VT>::SLACK> lay(smem);
-        K* so = lay.sk;
-        const int ph = phase16(gout);
+    // Compact the kept sources into the index array (the staged windows
+    // stay where they are; only indices move).
+    uint16_t* sidx = v.sidx;
+    int pos = (int)scan[warp] + incl - c;
 #pragma unroll
-        for (int i = 0; i < VT; ++i) {
-            if (keep & (1u << i)) so[ph + pos++] = keys[i];
-        }
-        __syncthreads();
-        K* gbase = gout - ph;  // 16-byte aligned
-        const int end = ph + n_out;
-        const int q0 = ph > 0 ? 1 : 0, q1 = end / EK;  // whole vectors [q0, q1)
-        for (int q = q0 + tid; q < q1; q += NT)
-            st_global_cs_v4(gbase + q * EK, *reinterpret_cast<const uint4*>(so + q * EK));
-        // The elements outside whole vectors: [ph, q0 * EK) and [max(q1 * EK, ph), end).
-        const int head_end = q0 * EK < end ? q0 * EK : end;
-        if (tid < head_end - ph) gbase[ph + tid] = so[ph + tid];
-        const int tail0 = q1 * EK > ph ? q1 * EK : ph;
-        if (q1 >= q0 && tid < end - tail0 && tail0 >= head_end) gbase[tail0 + tid] = so[tail0 + tid];
-    } else {
-        // Compact the kept sources into the index array (the staged windows
-        // stay where they are; only indices move).
-        uint16_t* sidx = v.sidx;
-        int pos = (int)scan[warp] + incl - c;
-#pragma unroll
-        for (int i = 0; i < VT; ++i) {
-            if (keep & (1u << i)) sidx[pos++] = (uint16_t)((packed[i / 2] >> (16 * (i & 1))) & 0xFFFF);
-        }
-        __syncthreads();
-        K* gout = ta.out + g;
-        for (int j = tid; j < n_out; j += NT) {
-            const int s = sidx[j];
-            gout[j] = s < t.la ? v.sA[s] : v.sB[s - t.la];
-        }
-        uint32_t* gvout = ta.outv + g;
-        for (int j = tid; j < n_out; j += NT) {
-            const int s = sidx[j];
-            gvout[j] = s < t.la ? v.vA[s] : v.vB[s - t.la];
-        }
+    for (int i = 0; i < VT; ++i) {
+        if (keep & (1u << i)) sidx[pos++] = (uint16_t)((packed[i / 2] >> (16 * (i & 1))) & 0xFFFF);
+    }
+    __syncthreads();
+    K* gout = ta.out + g;
+    for (int j = tid; j < n_out; j += NT) {
+        const int s = sidx[j];
+        gout[j] = s < t.la ? v.sA[s] : v.sB[s - t.la];
+    }
+    uint32_t* gvout = ta.outv + g;
+    for (int j = tid; j < n_out; j += NT) {
+        const int s = sidx[j];
+        gvout[j] = s < t.la ? v.vA[s] : v.vB[s - t.la];
     }
     if (tid == 0 && tile == p.ntiles - 1) *p.count = g + n_out;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent set-operation kernel for keys alone.  Each CTA runs tiles of
+// the single pass through a ring of three shared-memory buffers, with three
+// warp roles working on different tiles at once:
+//   stager  (one warp): takes the next tile from the counter, and once a
+//           buffer is free starts the TMA copies of the tile's windows into
+//           it and loads the keys next to the windows;
+//   walkers (NT threads): wait for a staged tile, split it (Thm 17), walk
+//           and decide its outputs, publish its kept count, compact the kept
+//           keys over the windows of the same buffer (which the walk no
+//           longer needs), then write the previous tile's compacted keys to
+//           the offset the look-back warp has found meanwhile, and free
+//           that buffer;
+//   look-back (one warp): for each walked tile, adds up the published
+//           counts of the tiles before it (decoupled look-back) and
+//           publishes its inclusive prefix.
+// So the copies of later tiles and the look-back of the last one overlap the
+// walk, where a CTA per tile waited for each in turn.  Hand-offs are
+// mbarriers, one set per buffer (the k-th tile uses buffer k % 3 and waits
+// for phase parity (k / 3) & 1); every wait is bounded.  Walkers synchronise
+// among themselves with named barrier 1 only.
+// ---------------------------------------------------------------------------
+template <class K>
+struct __align__(16) PSetInfo {
+    TilePlace<K> t;
+    SetCtx<K> x;
+    int64_t tile;  // -1: no more tiles
+};
+
+constexpr int PSET_NB = 3;  // buffers in the ring
+
+template <class K, int NT, int VT>
+struct PSetSmem {
+    static constexpr int T = NT * VT;
+    static constexpr int EK = 16 / sizeof(K);
+    // Windows (at their 16-byte phases), then spare slots: the end-test-free
+    // walk reads up to VT + 1 past its start.  The compacted output (<= T
+    // keys) later takes the buffer from its start; its store reads up to two
+    // words past its end.
+    static constexpr int SLACK = VT + 1;
+    static constexpr size_t buf_bytes = ((size_t)(T + 3 * EK + SLACK) * sizeof(K) + 15) / 16 * 16;
+    static constexpr size_t info_off = PSET_NB * buf_bytes;
+    static constexpr size_t info_bytes = (sizeof(PSetInfo<K>) + 15) / 16 * 16;
+    static constexpr size_t scan_off = info_off + PSET_NB * info_bytes;
+    static constexpr size_t split_off = scan_off + (NT / 32) * 8;
+    static constexpr size_t slot_off = split_off + NT * 4;  // per buffer: {tile, kept, prefix}
+    static constexpr size_t bar_off = slot_off + PSET_NB * 24;
+    static constexpr size_t bytes = bar_off + 4 * PSET_NB * 8;  // full, walked, placed, freed [NB]
+};
+
+constexpr uint32_t PSET_WAIT_LIMIT = 1u << 22;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t tx)
+{
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(tx)
+                 : "memory");
+}
+
+// Named barrier 1 over the NT walker threads.
+template <int NT>
+__device__ __forceinline__ void walker_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+}
+
+template <int NT>
+__device__ __forceinline__ bool walker_sync_and(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred a, b;\n\t"
+        "setp.ne.u32 a, %1, 0;\n\t"
+        "bar.red.and.pred b, 1, %2, a;\n\t"
+        "selp.u32 %0, 1, 0, b;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(NT)
+        : "memory");
+    return r != 0;
+}
+
+// Copies nw 32-bit words from shared memory (16-byte aligned) to global
+// memory at any 4-byte phase: whole 16-byte vectors assembled from two
+// aligned shared vectors, the partial vectors at both ends word by word.
+// Reads up to two words past nw.
+template <int NT>
+__device__ __forceinline__ void store_words_shifted(const uint32_t* so, int nw, uint32_t* gw, int tid)
+{
+    const int pw = (int)(((uintptr_t)gw >> 2) & 3);
+    uint32_t* gbase = gw - pw;  // 16-byte aligned
+    const int end = pw + nw;
+    const int q0 = pw ? 1 : 0, q1 = end >> 2;  // whole vectors [q0, q1) of gbase
+    if (pw == 0) {
+        for (int q = tid; q < q1; q += NT)
+            st_global_cs_v4(gbase + 4 * q, *reinterpret_cast<const uint4*>(so + 4 * q));
+    } else {
+        for (int q = q0 + tid; q < q1; q += NT) {
+            // Global word 4q is local word 4q - pw.
+            const uint4 a = *reinterpret_cast<const uint4*>(so + 4 * q - 4);
+            const uint4 c = *reinterpret_cast<const uint4*>(so + 4 * q);
+            uint4 r;
+            if (pw == 1) r = make_uint4(a.w, c.x, c.y, c.z);
+            else if (pw == 2) r = make_uint4(a.z, a.w, c.x, c.y);
+            else r = make_uint4(a.y, a.z, a.w, c.x);
+            st_global_cs_v4(gbase + 4 * q, r);
+        }
+    }
+    const int head_end = 4 * q0 < end ? 4 * q0 : end;
+    if (tid < head_end - pw) gbase[pw + tid] = so[tid];
+    const int tail0 = 4 * q1 > head_end ? 4 * q1 : head_end;
+    if (tid < end - tail0) gbase[tail0 + tid] = so[tail0 - pw + tid];
+}
+
+template <class K, int NT, int VT>
+struct PSetView {
+    unsigned char* smem;
+    __device__ __forceinline__ K* buf(int b) const
+    {
+        return reinterpret_cast<K*>(smem + b * PSetSmem<K, NT, VT>::buf_bytes);
+    }
+    __device__ __forceinline__ PSetInfo<K>& info(int b) const
+    {
+        return *reinterpret_cast<PSetInfo<K>*>(smem + PSetSmem<K, NT, VT>::info_off +
+                                                b * PSetSmem<K, NT, VT>::info_bytes);
+    }
+    // set 0 full (stager -> walkers), 1 walked (walkers -> look-back),
+    // 2 placed (look-back -> walkers), 3 freed (walkers -> stager)
+    __device__ __forceinline__ uint64_t* bar(int set, int b) const
+    {
+        return reinterpret_cast<uint64_t*>(smem + PSetSmem<K, NT, VT>::bar_off) + set * PSET_NB + b;
+    }
+    __device__ __forceinline__ int64_t* slot(int b) const
+    {
+        return reinterpret_cast<int64_t*>(smem + PSetSmem<K, NT, VT>::slot_off) + 3 * b;
+    }
+};
+
+// Stager: the ring position k's tile (taken before its buffer is free, so
+// its split points are loaded while waiting).
+template <class K, int NT, int VT>
+__device__ __forceinline__ void pset_stager(const SetArgs<K>& p, unsigned char* smem, unsigned int* err)
+{
+    using SM = PSetSmem<K, NT, VT>;
+    constexpr int EK = 16 / sizeof(K);
+    const PSetView<K, NT, VT> sv{smem};
+    const int lane = threadIdx.x & 31;
+    const TileArgs<K>& ta = p.t;
+    for (int k = 0;; ++k) {
+        const int b = k % PSET_NB;
+        unsigned int tk = 0;
+        if (lane == 0) tk = atomicAdd(p.tile_counter, 1u);
+        const int64_t tile = (int64_t)__shfl_sync(0xFFFFFFFFu, tk, 0);
+        const bool last = tile >= p.ntiles;
+        TilePlace<K> t;
+        if (!last) t = tile_place(ta, tile, SM::T, ta.a_split);
+        if (k >= PSET_NB &&
+            !mbar_wait_bounded(sv.bar(3, b), ((k - PSET_NB) / PSET_NB) & 1, PSET_WAIT_LIMIT)) {
+            // The buffer was never freed: stop staging.
+            if (lane == 0) atomicOr(err, MP_KERR_MBAR_TIMEOUT);
+            return;
+        }
+        PSetInfo<K>& in = sv.info(b);
+        uint64_t* full = sv.bar(0, b);
+        if (last) {
+            if (lane == 0) in.tile = -1;
+            mbar_arrive(full);
+            return;
+        }
+        const auto v = stage_view<K, false, NT, VT>(t, sv.buf(b), nullptr, nullptr);
+        if (lane == 0) {
+            in.tile = tile;
+            in.t = t;
+            mbar_expect_tx(full, interior_bytes(t.gA, t.la) + interior_bytes(t.gB, t.lb));
+            issue_interior(v.sA, t.gA, t.la, full);
+            issue_interior(v.sB, t.gB, t.lb, full);
+        }
+        if (lane < 4 * EK) {
+            const EdgeLoad<K> e = edge_load(lane, t.gA, t.la, t.gB, t.lb);
+            if (e.dst >= 0) (e.in_b ? v.sB : v.sA)[e.dst] = e.val;
+        }
+        // The keys just outside the windows.
+        const int64_t a0 = t.gA - ta.a, b0 = t.gB - ta.b, a1 = a0 + t.la, b1 = b0 + t.lb;
+        SetCtx<K>& x = in.x;
+        if (lane == 28) {
+            x.has_prev_a = a0 > 0;
+            if (a0 > 0) x.prev_a = ld_global_nc(ta.a + a0 - 1);
+        } else if (lane == 29) {
+            x.has_prev_b = b0 > 0;
+            if (b0 > 0) x.prev_b = ld_global_nc(ta.b + b0 - 1);
+        } else if (lane == 30) {
+            x.has_next_b = b1 < ta.nb;
+            if (b1 < ta.nb) x.next_b = ld_global_nc(ta.b + b1);
+        } else if (lane == 31) {
+            x.has_next_a = a1 < ta.na;
+            if (a1 < ta.na) x.next_a = ld_global_nc(ta.a + a1);
+        }
+        mbar_arrive(full);  // every lane: its writes are released with the phase
+    }
+}
+
+// Look-back warp: the place of each walked tile.
+template <class K, int NT, int VT>
+__device__ __forceinline__ void pset_lookback(const SetArgs<K>& p, unsigned char* smem, unsigned int* err)
+{
+    const PSetView<K, NT, VT> sv{smem};
+    const int lane = threadIdx.x & 31;
+    for (int k = 0;; ++k) {
+        const int b = k % PSET_NB;
+        if (!mbar_wait_bounded(sv.bar(1, b), (k / PSET_NB) & 1, PSET_WAIT_LIMIT)) {
+            if (lane == 0) atomicOr(err, MP_KERR_MBAR_TIMEOUT);
+            return;
+        }
+        const int64_t tile = sv.slot(b)[0], n = sv.slot(b)[1];
+        if (tile < 0) return;
+        const unsigned long long pre = tile > 0 ? lookback(p.status, tile, lane, err) : 0ull;
+        if (lane == 0) {
+            if (tile > 0) st_relaxed_u64(p.status + tile, LB_INC | (pre + (unsigned long long)n));
+            if (tile == p.ntiles - 1) *p.count = (int64_t)pre + n;
+            sv.slot(b)[2] = (int64_t)pre;
+            mbar_arrive(sv.bar(2, b));
+        }
+        __syncwarp();
+    }
+}
+
+// Walkers: tile j's compacted keys leave for their place (once the
+// look-back warp has found it) and its buffer is freed.
+template <class K, int NT, int VT>
+__device__ __forceinline__ void pset_place(const SetArgs<K>& p, const PSetView<K, NT, VT>& sv, int j,
+                                           unsigned int* err, int tid)
+{
+    constexpr int WPK = (int)sizeof(K) / 4;  // 32-bit words per key
+    const int b = j % PSET_NB;
+    if (walker_sync_and<NT>(mbar_wait_bounded(sv.bar(2, b), (j / PSET_NB) & 1, PSET_WAIT_LIMIT))) {
+        const int64_t g = sv.slot(b)[2], n = sv.slot(b)[1];
+        if (g + n > p.cap) {
+            if (tid == 0) atomicOr(err, MP_KERR_SETOP);
+        } else {
+            store_words_shifted<NT>(reinterpret_cast<const uint32_t*>(sv.buf(b)), (int)n * WPK,
+                                    reinterpret_cast<uint32_t*>(p.t.out + g), tid);
+        }
+    } else if (tid == 0) {
+        atomicOr(err, MP_KERR_LOOKBACK);
+    }
+    mbar_arrive(sv.bar(3, b));  // every walker, after its reads of the buffer
+}
+
+template <class K, int NT, int VT, int CK>
+__device__ __forceinline__ void pset_walkers(const SetArgs<K>& p, unsigned char* smem, unsigned int* err)
+{
+    using SM = PSetSmem<K, NT, VT>;
+    constexpr int NW = NT / 32;
+    const PSetView<K, NT, VT> sv{smem};
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned long long* scan = reinterpret_cast<unsigned long long*>(smem + SM::scan_off);
+    int* split = reinterpret_cast<int*>(smem + SM::split_off);
+    const TileArgs<K>& ta = p.t;
+    // err[1]: the staging-wait fault switch (see bulk_stage).
+    const uint32_t first_limit = __ldcg(err + 1) ? 0u : PSET_WAIT_LIMIT;
+    int k = 0;
+    for (;; ++k) {
+        const int b = k % PSET_NB;
+        const uint32_t par = (k / PSET_NB) & 1;
+        const bool ok = walker_sync_and<NT>(mbar_wait_bounded(sv.bar(0, b), par, first_limit));
+        if (!ok) {
+            if (tid == 0) atomicOr(err, MP_KERR_MBAR_TIMEOUT);
+            // Give copies in flight a bounded time to land; if they do not,
+            // stop here (the tile, if any, is never published).
+            if (!walker_sync_and<NT>(mbar_wait_bounded(sv.bar(0, b), par, PSET_WAIT_LIMIT))) break;
+        }
+        PSetInfo<K>& in = sv.info(b);
+        const int64_t tile = in.tile;
+        if (tile < 0) break;
+        const TilePlace<K> t = in.t;
+        SetCtx<K>& x = in.x;
+        K keys[VT];
+        uint32_t keep = 0;
+        if (ok) {  // a tile whose staging wait failed is published as empty
+            const auto v = stage_view<K, false, NT, VT>(t, sv.buf(b), nullptr, nullptr);
+            const int64_t a0 = t.gA - ta.a, b0 = t.gB - ta.b, b1 = b0 + t.lb;
+            const int la = t.la, lb = t.lb, L = la + lb;
+            // Runs crossing a window edge (as in setop_tile_walk).
+            const bool b0_rep =
+                lb > 0 && ((lb > 1 && v.sB[1] == v.sB[0]) || (x.has_prev_b && x.prev_b == v.sB[0]));
+            const bool a_end_rep = la > 0 && ((la > 1 && v.sA[la - 2] == v.sA[la - 1]) ||
+                                              (la == 1 && x.has_prev_a && x.prev_a == v.sA[0]));
+            const bool need_a =
+                x.has_prev_a && ((la > 0 && v.sA[0] == x.prev_a) || (b0_rep && v.sB[0] == x.prev_a));
+            const bool need_b = x.has_prev_b && lb > 0 && v.sB[0] == x.prev_b;
+            const bool need_n = x.has_next_b &&
+                                ((lb > 0 && v.sB[lb - 1] == x.next_b) || (a_end_rep && v.sA[la - 1] == x.next_b));
+            if (need_a || need_b || need_n) {
+                if (warp == 3) {
+                    if (lane == 0 && need_a) x.lb_prev_a = run_start(ta.a, a0 - 1);
+                    if (lane == 1 && need_b) x.lb_prev_b = run_start(ta.b, b0 - 1);
+                    if (lane == 2 && need_n) x.ub_next_b = run_end(ta.b, ta.nb, b1);
+                }
+                walker_sync<NT>();
+            }
+            const int diag = tid * VT < L ? tid * VT : L;
+            const int ai = smem_diagonal_search_ck<CK>(v.sA, la, v.sB, lb, diag, ta.codec);
+            split[tid] = ai;
+            walker_sync<NT>();
+            const int dend = diag + VT;
+            const int ai_end = tid + 1 < NT ? split[tid + 1] : la;
+            const bool inside = dend < L && ai_end < la && dend - ai_end < lb;
+            keep = setop_walk_keys<K, VT, CK, true>(v.sA, la, v.sB, lb, ai, diag - ai, L - diag, inside, p.op,
+                                                     x, a0, b0, ta.codec, keys);
+        }
+        const int c = __popc(keep);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) scan[warp] = (unsigned long long)incl;
+        walker_sync<NT>();  // every walk is done (the windows are dead); warp totals visible
+        // Every warp scans the warp totals itself.
+        const unsigned long long w = lane < NW ? scan[lane] : 0;
+        unsigned long long wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        const unsigned long long total = __shfl_sync(0xFFFFFFFFu, wi, NW - 1);
+        const int base = (int)__shfl_sync(0xFFFFFFFFu, wi - w, warp);
+        if (tid == 0) {
+            st_relaxed_u64(p.status + tile, (tile == 0 ? LB_INC : LB_AGG) | total);
+            sv.slot(b)[0] = tile;
+            sv.slot(b)[1] = (int64_t)total;
+            mbar_arrive(sv.bar(1, b));
+        }
+        // The kept keys replace the windows, from the buffer's start.
+        K* so = sv.buf(b);
+        int pos = base + incl - c;
+#pragma unroll
+        for (int i = 0; i < VT; ++i) {
+            if (keep & (1u << i)) so[pos++] = keys[i];
+        }
+        if (k > 0) pset_place<K, NT, VT>(p, sv, k - 1, err, tid);
+    }
+    // No more tiles (or a failed copy): release the look-back warp, place
+    // the last tile.
+    if (tid == 0) {
+        sv.slot(k % PSET_NB)[0] = -1;
+        mbar_arrive(sv.bar(1, k % PSET_NB));
+    }
+    if (k > 0) pset_place<K, NT, VT>(p, sv, k - 1, err, tid);
+}
+
+template <class K, int NT, int VT, int CK, int MINB>
+__global__ void __launch_bounds__(NT + 64, MINB) setop_keys_kernel(SetArgs<K> p, unsigned int* err)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (threadIdx.x == 0) {
+        const PSetView<K, NT, VT> sv{smem};
+        for (int b = 0; b < PSET_NB; ++b) {
+            mbar_init(sv.bar(0, b), 32);  // full: the stager's lanes (+ the copies' bytes)
+            mbar_init(sv.bar(1, b), 1);   // walked: walker 0, with the tile's kept count
+            mbar_init(sv.bar(2, b), 1);   // placed: look-back lane 0, with the prefix
+            mbar_init(sv.bar(3, b), NT);  // freed: every walker, after the store
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int warp = threadIdx.x >> 5;
+    if (warp < NT / 32)
+        pset_walkers<K, NT, VT, CK>(p, smem, err);
+    else if (warp == NT / 32)
+        pset_stager<K, NT, VT>(p, smem, err);
+    else
+        pset_lookback<K, NT, VT>(p, smem, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -787,19 +1041,23 @@ __global__ void __launch_bounds__(NT, (sizeof(K) == 4 ? 1024 : 512) / NT)
 // ---------------------------------------------------------------------------
 // Tile shape per mode.  Items per thread: one bit each in the walk's masks,
 // so at most 32; an odd count starts the threads' walks in different
-// shared-memory banks (two sets of 2^27 keys: uint32 union 1.50 -> 1.25 ms
-// at 31, int64 union 1.47 -> 1.06 ms at 15; with values 27 beats 31).
-// 16-byte keys keep 8.  Threads: 512 for tiles without values (fewer, larger
-// tiles shorten the look-back: uint32 union 0.82 ms with 256 threads, 0.81
-// with 512, 0.85 with 128), 256 with values (1.28 ms against 1.57 with 512).
+// shared-memory banks.  Tiles with values (one per CTA): 256 threads x 27
+// outputs for 4-byte keys (1.28 ms for the union of two 2^27-key sets
+// against 1.57 with 512 threads), 15 for 8-byte keys, 8 for 16-byte keys.
+// Keys alone (the persistent kernel; its three buffers of a tile each, two
+// CTAs per SM, bound the tile): 384 walkers x 23 for 4-byte keys (uint32
+// union 0.678 ms; 256 x 31: 0.687; 512 x 31 with one CTA per SM: 0.710;
+// 256 x 15 with three CTAs: 0.838), 256 x 15 for 8-byte and 256 x 8 for
+// 16-byte keys.
 constexpr int set_vt(int key_bytes, bool vals)
 {
-    return key_bytes == 4 ? (vals ? 27 : 31) : (key_bytes == 8 ? 15 : 8);
+    return key_bytes == 4 ? (vals ? 27 : 23) : (key_bytes == 8 ? 15 : 8);
 }
 
-constexpr int set_nt(bool vals) { return vals ? 256 : 512; }
+constexpr int set_nt(int key_bytes, bool vals) { return vals ? 256 : (key_bytes == 4 ? 384 : 256); }
+constexpr int PSET_MINB = 2;  // persistent keys-alone kernel: CTAs per SM
 
-int64_t setop_tile(int key_bytes, bool vals) { return (int64_t)set_nt(vals) * set_vt(key_bytes, vals); }
+int64_t setop_tile(int key_bytes, bool vals) { return (int64_t)set_nt(key_bytes, vals) * set_vt(key_bytes, vals); }
 
 template <class K, bool VALS, int CK>
 static cudaError_t launch_setop_ck(const MergeProblem& mp_, int op, const int64_t* splits,
@@ -807,14 +1065,24 @@ static cudaError_t launch_setop_ck(const MergeProblem& mp_, int op, const int64_
                                    int64_t* count, cudaStream_t stream)
 {
     constexpr int VT = set_vt((int)sizeof(K), VALS);
-    constexpr int NT = set_nt(VALS);
-    using SM = SetSmem<K, VALS, NT, VT>;
-    auto kern = setop_kernel<K, VALS, NT, VT, CK>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
+    constexpr int NT = set_nt((int)sizeof(K), VALS);
+    constexpr size_t smem_bytes = VALS ? SetSmem<K, VALS, NT, VT>::bytes : PSetSmem<K, NT, VT>::bytes;
+    void (*kern)(SetArgs<K>, unsigned int*);
+    if constexpr (VALS)
+        kern = setop_kernel<K, VALS, NT, VT, CK>;
+    else
+        kern = setop_keys_kernel<K, NT, VT, CK, PSET_MINB>;
+    static int resident = 0;  // CTAs per SM x SMs (persistent kernel)
+    if (!resident) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
         if (e != cudaSuccess) return e;
-        configured = true;
+        int dev = 0, sms = 0, per_sm = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, VALS ? NT : NT + 64, smem_bytes);
+        if (e != cudaSuccess) return e;
+        resident = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
     }
     unsigned int* err = kernel_error_word();
     if (!err) return cudaErrorInvalidSymbol;
@@ -839,9 +1107,9 @@ static cudaError_t launch_setop_ck(const MergeProblem& mp_, int op, const int64_
     a.tile_counter = tile_counter;
     a.count = count;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)a.ntiles);
-    cfg.blockDim = dim3(NT);
-    cfg.dynamicSmemBytes = SM::bytes;
+    cfg.gridDim = dim3((unsigned)(VALS ? a.ntiles : std::min<int64_t>(a.ntiles, resident)));
+    cfg.blockDim = dim3(VALS ? NT : NT + 64);
+    cfg.dynamicSmemBytes = smem_bytes;
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
