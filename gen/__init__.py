@@ -22,6 +22,9 @@ Workloads (sizes are parameters so that tests can run scaled-down copies):
                    orders: random, sorted, reverse, distinct256
 * ``batched``      many int32 merge pairs, per-side length floor(2^U),
                    U ~ Uniform[0, log2_max], each side uniform [0, 2^31), sorted
+* ``sets``         two duplicate-free int32 sets: each key of [0, 2^u) is in A
+                   with probability 1/2 and, independently, in B with
+                   probability 1/2 (adjacency-list-like sets sharing half)
 """
 from __future__ import annotations
 
@@ -198,6 +201,23 @@ def batched(n_seg: int = 16384, log2_max: float = 18.0, seed: int = BASE_SEED,
     av = np.arange(a.size, dtype=np.uint32)
     bv = np.arange(a.size, a.size + b.size, dtype=np.uint64).astype(np.uint32)
     return a, a_off, b, b_off, av, bv
+
+
+# --------------------------------------------------------------------------
+# Set-operation inputs.
+# --------------------------------------------------------------------------
+
+def sets(log2_universe: int = 28, seed: int = BASE_SEED):
+    """(a, b): the keys of [0, 2^log2_universe) whose membership bit is set,
+    one independent fair bit per key and side (streams 51 and 52), ascending
+    int32."""
+    words = max(1, (1 << log2_universe) // 64)
+
+    def side(stream):
+        bits = np.unpackbits(splitmix64(seed, stream, words).view(np.uint8), bitorder="little")
+        return np.flatnonzero(bits[: 1 << log2_universe]).astype(np.int32)
+
+    return side(51), side(52)
 
 
 # --------------------------------------------------------------------------

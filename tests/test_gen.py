@@ -69,3 +69,10 @@ def test_workload_shapes():
         seg = a[a_off[s_]:a_off[s_ + 1]]
         assert np.all(seg[1:] >= seg[:-1])
         assert 1 <= seg.size <= 256
+
+    a, b = gen.sets(log2_universe=16)
+    assert a.dtype == np.int32 and np.all(np.diff(a) > 0) and np.all(np.diff(b) > 0)
+    assert 0 <= a.min() and max(a.max(), b.max()) < (1 << 16)
+    # Independent fair bits: each side and the overlap near 1/2 and 1/4 of the universe.
+    assert abs(a.size - 32768) < 1000 and abs(b.size - 32768) < 1000
+    assert abs(np.intersect1d(a, b).size - 16384) < 800

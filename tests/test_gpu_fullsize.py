@@ -9,6 +9,9 @@ bench times (automatic plans, default stream).
   the whole output against the oracle's per-segment merge;
 * an int32 merge of 2^31 + 4097 outputs (past every 32-bit offset): the
   whole output and the split points past 2^31 against the oracle;
+* set operations on two duplicate-free sets of about 2^27 int32 keys each
+  sharing half (universe 2^28): all four operations on keys alone and the
+  union with values, the whole output against the oracle's;
 * sort of 2^28 keys (int32 and float32, four orders): properties that hold
   at any size -- the output is ascending under the key order (float: -0.0
   before +0.0) and is a permutation of the input (same multiset of bit
@@ -74,6 +77,28 @@ def _sorted_int32_with_ties(seed: int, n: int, start: int, max_gap: int) -> np.n
     x += start
     assert x[-1] < 2**31
     return x.astype(np.int32)
+
+
+def test_set_operations_full_size():
+    a, b = gen.sets()
+    assert a.size > 1.3e8 and b.size > 1.3e8
+    A, B = to_dev(a), to_dev(b)
+    for op in ["union", "intersection", "difference", "symmetric_difference"]:
+        k, _, _ = mp.mp_set_operation(op, A, B)
+        got = to_host(k, np.int32)
+        del k
+        ek, _ = oracle.set_op(op, a, b)
+        assert first_mismatch(got, ek) is None, op
+    av = np.arange(a.size, dtype=np.uint32)
+    bv = np.arange(a.size, a.size + b.size, dtype=np.uint64).astype(np.uint32)
+    k, v, _ = mp.mp_set_operation("union", A, B, vals_to_dev(av), vals_to_dev(bv))
+    got_k, got_v = to_host(k, np.int32), to_host(v, np.uint32)
+    del k, v, A, B
+    torch.cuda.empty_cache()
+    ek, ev = oracle.set_op("union", a, b, av, bv)
+    assert first_mismatch(got_k, ek) is None
+    assert first_mismatch(got_v, ev) is None
+    assert mp.mp_kernel_status(reset=True) == mp.MP_OK
 
 
 def test_merge_above_2e31_outputs():
