@@ -117,8 +117,7 @@ struct SetSmem {
     using B = BulkSmem<K, VALS, NT, VT, true>;
     static constexpr size_t ctx_off = (B::bytes + 15) / 16 * 16;
     static constexpr size_t scan_off = ctx_off + (sizeof(SetCtx<K>) + 15) / 16 * 16;
-    static constexpr size_t split_off = scan_off + (NT / 32 + 4) * 8;  // NT thread splits
-    static constexpr size_t bytes = split_off + NT * 4;
+    static constexpr size_t bytes = scan_off + (NT / 32 + 4) * 8;
 };
 
 // Order test of two stored keys under a codec kind: unsigned keys compare
@@ -328,13 +327,11 @@ __device__ __noinline__ bool setop_exact(bool from_a, K v, int ai, int bi, const
 // repeated keys and is decided exactly (setop_exact).  The outputs just
 // before and after the thread's share come from the windows or, at the
 // tile's edges, from the keys next to the windows.
-// KEEP: the merged keys are kept in out[] (the emit pass); without it (the
-// count pass) only the bit masks are built.
-template <class K, int VT, int CK, bool KEEP>
+template <class K, int VT, int CK>
 __device__ __forceinline__ uint32_t setop_walk_keys(const K* sA, int la, const K* sB, int lb, int ai, int bi,
                                                     int n_valid, bool inside, int op, const SetCtx<K>& x,
                                                     int64_t a0, int64_t b0, Codec<K> c,
-                                                    K (&out)[KEEP ? VT : 1])
+                                                    K (&out)[VT])
 {
     static_assert(VT <= 32, "one bit per output");
     const int ai0 = ai, bi0 = bi;
@@ -356,7 +353,7 @@ __device__ __forceinline__ uint32_t setop_walk_keys(const K* sA, int la, const K
         for (int i = 0; i < VT; ++i) {
             const bool take_a = !key_gt_ck<CK>(ka, kb, c);
             const K v = take_a ? ka : kb;
-            if constexpr (KEEP) out[i] = v;
+            out[i] = v;
             took |= (uint32_t)take_a << i;
             eqp |= (uint32_t)(v == last) << i;
             last = v;
@@ -369,7 +366,7 @@ __device__ __forceinline__ uint32_t setop_walk_keys(const K* sA, int la, const K
         for (int i = 0; i < VT; ++i) {
             const bool take_a = (bi >= lb) || (ai < la && !key_gt_ck<CK>(ka, kb, c));
             const K v = take_a ? ka : kb;
-            if constexpr (KEEP) out[i] = v;
+            out[i] = v;
             took |= (uint32_t)take_a << i;
             eqp |= (uint32_t)(v == last) << i;
             last = v;
@@ -965,7 +962,7 @@ __device__ __forceinline__ void pset_walkers(const SetArgs<K>& p, unsigned char*
             const int dend = diag + VT;
             const int ai_end = tid + 1 < NT ? split[tid + 1] : la;
             const bool inside = dend < L && ai_end < la && dend - ai_end < lb;
-            keep = setop_walk_keys<K, VT, CK, true>(v.sA, la, v.sB, lb, ai, diag - ai, L - diag, inside, p.op,
+            keep = setop_walk_keys<K, VT, CK>(v.sA, la, v.sB, lb, ai, diag - ai, L - diag, inside, p.op,
                                                      x, a0, b0, ta.codec, keys);
         }
         const int c = __popc(keep);
