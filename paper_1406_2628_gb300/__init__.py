@@ -457,9 +457,22 @@ def mp_merge_batched(a, a_off, b, b_off, out=None, a_vals=None, b_vals=None, out
 def mp_merge_grouped(problems, with_values: bool = False, stream=None):
     """Merge many independent problems in one launch.  problems: list of
     (a_keys, b_keys, out_keys) or (a_keys, a_vals, b_keys, b_vals, out_keys,
-    out_vals) tuples of device tensors (one key width for all)."""
+    out_vals) tuples of device tensors (one key width for all), or the
+    descriptor array mp_merge_grouped_descs built from such a list (the
+    tensors must stay alive)."""
+    if isinstance(problems, ctypes.Array):
+        _check(lib().mp_merge_grouped(problems, len(problems), 1 if with_values else 0, _stream(stream)))
+        return
+    arr = mp_merge_grouped_descs(problems, with_values)
+    _check(lib().mp_merge_grouped(arr, len(problems), 1 if with_values else 0, _stream(stream)))
+
+
+def mp_merge_grouped_descs(problems, with_values: bool = False):
+    """The C descriptor array of mp_merge_grouped for a list of problems
+    (building it walks the list in Python, which for many problems costs
+    more than the launch itself)."""
     n = len(problems)
-    arr = (mp_merge_desc * max(n, 1))()
+    arr = (mp_merge_desc * n)()
     for i, pr in enumerate(problems):
         if with_values:
             ak, av, bk, bv, ok, ov = pr
@@ -473,7 +486,7 @@ def mp_merge_grouped(problems, with_values: bool = False, stream=None):
         d.out_keys = _dev(ok, "out_keys")
         if with_values:
             d.a_vals, d.b_vals, d.out_vals = _vals(av, "a_vals"), _vals(bv, "b_vals"), _vals(ov, "out_vals")
-    _check(lib().mp_merge_grouped(arr, n, 1 if with_values else 0, _stream(stream)))
+    return arr
 
 
 def mp_check_sorted(keys, stream=None, descending: bool = False, wide: str | None = None) -> int:

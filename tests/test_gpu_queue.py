@@ -26,7 +26,8 @@ def _lib():
 @pytest.mark.parametrize("dts", [(np.int32, np.float32, np.uint32), (np.uint64, np.int64)],
                          ids=["w4", "w8"])
 @pytest.mark.parametrize("vals", [False, True])
-def test_merge_grouped(dts, vals):
+@pytest.mark.parametrize("prepared", [False, True], ids=["tuples", "descs"])
+def test_merge_grouped(dts, vals, prepared):
     rng = np.random.default_rng(1000)
     probs, expect = [], []
     sizes = [(0, 0), (1, 0), (0, 7), (5000, 3), (12_345, 54_321), (4096, 4096), (1, 1), (70_000, 1)]
@@ -44,7 +45,10 @@ def test_merge_grouped(dts, vals):
         else:
             probs.append((A, B, OK))
             expect.append((dt, *oracle.merge(a, b)))
-    mp.mp_merge_grouped(probs, with_values=vals)
+    if prepared:
+        mp.mp_merge_grouped(mp.mp_merge_grouped_descs(probs, with_values=vals), with_values=vals)
+    else:
+        mp.mp_merge_grouped(probs, with_values=vals)
     torch.cuda.synchronize()
     for pr, (dt, ek, ev) in zip(probs, expect):
         assert first_mismatch(to_host(pr[-2] if vals else pr[-1], dt), ek) is None
