@@ -212,3 +212,46 @@ def test_force_plan_override_of_automatic_plans(lib, monkeypatch):
     assert "MP_FORCE_PLAN" in mp.mp_last_error()
     monkeypatch.delenv("MP_FORCE_PLAN")
     assert mp.mp_merge_resolve_plan(mp.MP_U64, True, big) == auto
+
+
+def test_set_operation_and_grouped_host_errors(lib):
+    # Output capacities per operation (multiset semantics bound the result).
+    assert lib.mp_set_capacity(mp.MP_SET_UNION, 5, 7) == 12
+    assert lib.mp_set_capacity(mp.MP_SET_INTERSECTION, 5, 7) == 5
+    assert lib.mp_set_capacity(mp.MP_SET_DIFFERENCE, 5, 7) == 5
+    assert lib.mp_set_capacity(mp.MP_SET_SYMMETRIC_DIFFERENCE, 5, 7) == 12
+    assert lib.mp_set_capacity(9, 5, 7) == -1
+    assert lib.mp_set_capacity(mp.MP_SET_UNION, -1, 7) == -1
+    # Set operations: rejected on the host, before any CUDA call.
+    cnt = 0x9000
+    st = lib.mp_set_operation(9, mp.MP_I32, 0x1000, None, 1, 0x2000, None, 1, 0x3000, None, cnt, None)
+    assert st == mp.MP_ERR_INVALID_ARG
+    st = lib.mp_set_operation(mp.MP_SET_UNION, 17, 0x1000, None, 1, 0x2000, None, 1, 0x3000, None, cnt, None)
+    assert st == mp.MP_ERR_UNSUPPORTED_DTYPE
+    st = lib.mp_set_operation(mp.MP_SET_UNION, mp.MP_I32, 0x1000, None, 1, 0x2000, None, 1, 0x3000, None, None,
+                              None)
+    assert st == mp.MP_ERR_INVALID_ARG and "out_count" in mp.mp_last_error()
+    st = lib.mp_set_operation(mp.MP_SET_UNION, mp.MP_I32, 0x1000, None, 1, 0x2000, None, 1, 0x3000, None,
+                              cnt + 4, None)
+    assert st == mp.MP_ERR_INVALID_ARG and "aligned" in mp.mp_last_error()
+    st = lib.mp_set_operation(mp.MP_SET_UNION, mp.MP_I32, 0x1000, None, 100, 0x2000, None, 100, 0x1000, None,
+                              cnt, None)
+    assert st == mp.MP_ERR_INVALID_ARG and "overlap" in mp.mp_last_error()
+    # Grouped merges: descriptor array and key widths checked first.
+    assert lib.mp_merge_grouped(None, 0, 0, None) == mp.MP_OK
+    assert lib.mp_merge_grouped(None, 1, 0, None) == mp.MP_ERR_INVALID_ARG
+    assert lib.mp_merge_grouped(None, -1, 0, None) == mp.MP_ERR_INVALID_ARG
+    arr = (mp.mp_merge_desc * 2)()
+    for i, d in enumerate(arr):
+        d.dtype = mp.MP_I32
+        d.a_keys, d.na = 0x10000 + i * 0x1000, 4
+        d.b_keys, d.nb = 0x20000 + i * 0x1000, 4
+        d.out_keys = 0x30000 + i * 0x1000
+    arr[1].dtype = mp.MP_U64
+    assert lib.mp_merge_grouped(arr, 2, 0, None) == mp.MP_ERR_INVALID_ARG
+    assert "widths" in mp.mp_last_error()
+    arr[1].dtype = mp.MP_U128
+    assert lib.mp_merge_grouped(arr, 2, 0, None) == mp.MP_ERR_UNSUPPORTED_DTYPE
+    arr[1].dtype = mp.MP_I32
+    arr[1].out_keys = arr[1].a_keys  # output overlapping an input
+    assert lib.mp_merge_grouped(arr, 2, 0, None) == mp.MP_ERR_INVALID_ARG
