@@ -1042,16 +1042,16 @@ __global__ void __launch_bounds__(NT + 64, MINB) setop_keys_kernel(SetArgs<K> p,
 // outputs for 4-byte keys (1.28 ms for the union of two 2^27-key sets
 // against 1.57 with 512 threads), 15 for 8-byte keys, 8 for 16-byte keys.
 // Keys alone (the persistent kernel; its three buffers of a tile each, two
-// CTAs per SM, bound the tile): 384 walkers x 23 for 4-byte keys (uint32
-// union 0.678 ms; 256 x 31: 0.687; 512 x 31 with one CTA per SM: 0.710;
-// 256 x 15 with three CTAs: 0.838), 256 x 15 for 8-byte and 256 x 8 for
-// 16-byte keys.
+// CTAs per SM, bound the tile): 320 walkers x 27 for 4-byte keys (uint32
+// union 0.661 ms; 352 x 25: 0.669; 384 x 23: 0.676; 416 x 21, spilling:
+// 0.772; 256 x 31: 0.687; 512 x 31 with one CTA per SM: 0.710), 256 x 15
+// for 8-byte and 256 x 8 for 16-byte keys.
 constexpr int set_vt(int key_bytes, bool vals)
 {
-    return key_bytes == 4 ? (vals ? 27 : 23) : (key_bytes == 8 ? 15 : 8);
+    return key_bytes == 4 ? 27 : (key_bytes == 8 ? 15 : 8);
 }
 
-constexpr int set_nt(int key_bytes, bool vals) { return vals ? 256 : (key_bytes == 4 ? 384 : 256); }
+constexpr int set_nt(int key_bytes, bool vals) { return vals ? 256 : (key_bytes == 4 ? 320 : 256); }
 constexpr int PSET_MINB = 2;  // persistent keys-alone kernel: CTAs per SM
 
 int64_t setop_tile(int key_bytes, bool vals) { return (int64_t)set_nt(key_bytes, vals) * set_vt(key_bytes, vals); }
