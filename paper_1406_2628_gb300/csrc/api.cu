@@ -94,7 +94,7 @@ bool take_fault(int kind)
 
 mp_status scratch_alloc(void** ptr, size_t bytes, cudaStream_t stream)
 {
-    cudaMemPool_t pool;
+    cudaMemPool_t pool = nullptr;
     mp_status st = get_pool(&pool);
     if (st != MP_OK) return st;
     if (take_fault(MP_FAULT_SCRATCH_ALLOC)) {
